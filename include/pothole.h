@@ -1,0 +1,221 @@
+/*
+ * libpothole: GB300 (sm_103a) CUDA implementation of the stereo road pothole-detection path of
+ * Fan, Ozgunalp, Wang, Liu, Pitas, "Rethinking Road Surface 3D Reconstruction and Pothole Detection:
+ * From Perspective Transformation to Disparity Map Segmentation" (arXiv 2012.10802).
+ *
+ * The calls follow the paper's pipeline (Fig. 1 and Sec. II):
+ *   warp (Sec. II-A) -> cost -> aggregate -> disparity (Sec. II-B) -> transform (Sec. II-C)
+ *   -> superpixels (Sec. II-D) -> pothole mask (Sec. II-E).
+ *
+ * Conventions for every call:
+ *   - All image/volume pointers are DEVICE pointers owned by the caller unless a parameter says
+ *     "host".  Images are row-major; `pitch` is the row stride in bytes of a uint8 image (>= W).
+ *     Every other array is dense with no row padding.  Volumes are [H][W][D], disparity innermost.
+ *   - Work is enqueued on the context's stream and is asynchronous: outputs are valid once that
+ *     stream has reached the call (e.g. after cudaStreamSynchronize).  Host outputs are written
+ *     before the call returns.
+ *   - Arguments are validated before anything is launched; a bad argument returns
+ *     PD_ERR_INVALID_ARG and launches nothing.  A CUDA failure returns PD_ERR_CUDA.  In both cases
+ *     pd_last_error() gives a one-line reason.  The context stays usable after an error.
+ *   - The context owns its scratch memory.  It grows on demand (cudaMalloc, which synchronises the
+ *     device); failure returns PD_ERR_OOM and leaves the context valid.  Call a stage once outside
+ *     any CUDA-graph capture before capturing it, so the scratch already has its size.
+ *   - A context is not thread-safe: use one per host thread / stream.
+ *   - A disparity map value < 0 marks an invalid pixel.
+ */
+#ifndef POTHOLE_H
+#define POTHOLE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pd_ctx pd_ctx;
+
+typedef enum {
+  PD_OK = 0,
+  PD_ERR_INVALID_ARG = 1,
+  PD_ERR_OOM = 2,
+  PD_ERR_CUDA = 3,
+  PD_ERR_TIMEOUT = 4,
+  PD_ERR_UNSUPPORTED = 5
+} pd_status;
+
+/* Road disparity model of Sec. II-A, Eq. (3), with the roll applied about the image centre:
+ *   v' = (v - vc) cos(roll) - (u - uc) sin(roll) + vc,   uc = (W-1)/2, vc = (H-1)/2,
+ *   f(u, v) = a[0] + a[1] v' + a[2] v'^2   (a[2] is used only when order == 2).
+ * order 1 is the paper's linear model; order 2 adds the quadratic term. roll is in radians. */
+typedef struct {
+  int order;
+  double a[3];
+  double roll;
+} pd_road_model;
+
+/* Method parameters.  pd_default_params() fills the defaults given in brackets. */
+typedef struct {
+  int D;              /* disparity range searched after the warp [128]; multiple of 32, 32..256 */
+  int paths;          /* aggregation directions, 4 or 8 [8] */
+  int P1, P2;         /* Eq. (7)-(8) penalties lambda1 < lambda2 [4, 32]; 24 + P2 <= 255 */
+  int lr_tol;         /* left-right consistency tolerance in pixels [1] */
+  float delta_pt;     /* Eq. (6) margin delta_PT [10] */
+  float delta_dt;     /* Eq. (13) offset delta_DT [16] */
+  float delta_pd;     /* Eq. (14) tolerance delta_PD [2.36, the paper's value] */
+  int slic_K;         /* SLIC superpixel count [1000] */
+  float slic_m;       /* SLIC compactness [10] */
+  int slic_iters;     /* SLIC iterations [10] */
+  int model_order;    /* road model fitted by the transform, 1 or 2 [2] */
+  int threshold_mode; /* 0: t_s = road mean - delta_pd [0]; 1: t_s = t_r - delta_pd */
+} pd_params;
+
+/* Device-side outputs of pd_run_pipeline (all caller-owned device buffers; any may be NULL
+ * except where noted). */
+typedef struct {
+  int32_t* kappa;          /* [H] row shifts */
+  int16_t* d_int;          /* [H][W] integer disparity in the warped pair (required) */
+  float* D1;               /* [H][W] disparity w.r.t. the original pair, -1 = invalid (required) */
+  pd_road_model* fitted;   /* one fitted model (device) */
+  float* D2;               /* [H][W] transformed disparity (required) */
+  int32_t* labels;         /* [H][W] superpixel labels (required) */
+  float* D3;               /* [H][W] superpixel-clustered transformed disparity (required) */
+  double* thresholds;      /* [2]: t_r, t_s (device) */
+  uint8_t* mask;           /* [H][W] pothole mask (required) */
+} pd_outputs;
+
+/* Per-stage device times of the last pd_run_pipeline call, in milliseconds (host struct). */
+typedef struct {
+  float sgm_ms, transform_ms, superpixel_ms, mask_ms, total_ms;
+} pd_stage_times;
+
+/* ------------------------------------------------------------------------------ context */
+
+/* Creates a context on CUDA device `device` that enqueues on `stream` (a cudaStream_t; NULL means
+ * the legacy default stream).  The caller owns the stream. */
+pd_status pd_create(pd_ctx** ctx, int device, void* stream);
+/* Frees the context's scratch memory and the context.  NULL is accepted. */
+pd_status pd_destroy(pd_ctx* ctx);
+/* Changes the stream later calls enqueue on. */
+pd_status pd_set_stream(pd_ctx* ctx, void* stream);
+/* One-line description of the last error on this context ("" if none).  Valid until the next
+ * call on the context. */
+const char* pd_last_error(const pd_ctx* ctx);
+/* Fills *p with the defaults listed in pd_params. */
+pd_status pd_default_params(pd_params* p);
+/* Bytes of scratch the context currently holds. */
+size_t pd_workspace_bytes(const pd_ctx* ctx);
+
+/* ------------------------------------------------------------------- Sec. II-A: the warp */
+
+/* Eq. (6): kappa[v] = floor(min over x = 0..W-1 of f(x, v) - delta_pt), then the perspective
+ * transformation of the right image: right_warped(u, v) = right(clamp(u - kappa[v], 0, W-1), v),
+ * which makes the disparity w.r.t. (left, right_warped) equal to D1 - kappa (Eq. (10)).
+ * model: host pointer.  right, right_warped: uint8 [H] rows of `pitch` bytes (right_warped may be
+ * NULL to compute kappa only).  kappa: int32 [H]. */
+pd_status pd_warp(pd_ctx* ctx, const uint8_t* right, int W, int H, size_t pitch,
+                  const pd_road_model* model, float delta_pt, uint8_t* right_warped,
+                  int32_t* kappa);
+
+/* ------------------------------------------------------- Sec. II-B: matching cost c(p, d) */
+
+/* Eq. (7)'s matching cost c, which the paper does not define: a 5x5 census transform (24 bits;
+ * bit k, in raster order of the window without its centre, is set when that neighbour is darker
+ * than the centre; neighbours outside the image are clamped to the edge).
+ * img: uint8 rows of `pitch` bytes.  codes: uint32 [H][W]. */
+pd_status pd_census(pd_ctx* ctx, const uint8_t* img, int W, int H, size_t pitch, uint32_t* codes);
+
+/* c(p, d) = Hamming distance of the census codes of left(u, v) and right_warped(u - d, v), or 24
+ * when u - d < 0.  Inputs are uint8 images (rows of `pitch` bytes); cost: uint8 [H][W][D],
+ * 1 <= D <= 256. */
+pd_status pd_cost(pd_ctx* ctx, const uint8_t* left, const uint8_t* right_warped, int W, int H,
+                  size_t pitch, int D, uint8_t* cost);
+
+/* ------------------------------------------------------ Sec. II-B: aggregation, Eq. (8) */
+
+/* Eq. (8) along one direction r = (dx, dy), dx, dy in {-1, 0, 1}, not both 0:
+ *   L(p, d) = c(p, d) + min(L(p-r, d), L(p-r, d-1) + P1, L(p-r, d+1) + P1, m + P2) - m,
+ *   m = min_i L(p-r, i), and L = c where p - r is outside the image.
+ * Subtracting m (the printed equation omits it) changes every d of a pixel by the same amount.
+ * cost: uint8 [H][W][D]; L: uint8 [H][W][D].  D multiple of 32, 32..256. */
+pd_status pd_aggregate_dir(pd_ctx* ctx, const uint8_t* cost, int W, int H, int D, int dx, int dy,
+                           int P1, int P2, uint8_t* L);
+
+/* S(p, d) = sum of L over 4 directions {(1,0), (-1,0), (0,1), (0,-1)} or those plus the four
+ * diagonals.  cost: uint8 [H][W][D]; S: uint16 [H][W][D]. */
+pd_status pd_aggregate(pd_ctx* ctx, const uint8_t* cost, int W, int H, int D, int paths, int P1,
+                       int P2, uint16_t* S);
+
+/* ------------------------------------------------- Sec. II-B: disparity, Eqs. (9) and (10) */
+
+/* Eq. (9) winner-take-all d* = argmin_d S(p, d) (smallest d on ties); a parabola through
+ * S(d*-1), S(d*), S(d*+1) for 0 < d* < D-1 (one IEEE float division); the right-view
+ * disparity d_R(x) = argmin_{d : x+d < W} S(x+d, d); the pixel is valid when u >= D-1 (its
+ * whole search range lies in the image), u - d* >= 0 and |d* - d_R(u - d*)| <= lr_tol.  Then Eq. (10): D1 = d_sub + kappa[v] for valid pixels with a
+ * non-negative result, -1 otherwise.
+ * S: uint16 [H][W][D]; kappa: int32 [H]; d_int: int16 [H][W] (d*); D1: float [H][W]. */
+pd_status pd_disparity(pd_ctx* ctx, const uint16_t* S, int W, int H, int D, const int32_t* kappa,
+                       int lr_tol, int16_t* d_int, float* D1);
+
+/* The whole of Sec. II-A and II-B in one call (warp, census, cost, aggregation, disparity),
+ * without materialising S: the same results as the staged calls above.
+ * left, right: uint8 rows of `pitch` bytes; model, params: host pointers (params->D, paths, P1,
+ * P2, lr_tol, delta_pt are used); kappa (may be NULL): int32 [H]; d_int: int16 [H][W];
+ * D1: float [H][W]. */
+pd_status pd_sgm(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H,
+                 size_t pitch, const pd_road_model* model, const pd_params* params,
+                 int32_t* kappa, int16_t* d_int, float* D1);
+
+/* ----------------------------------------------------- Sec. II-C: disparity transformation */
+
+/* Exact sums the road fit needs over the pixels with D1 >= 0, with q = rint(1024 D1) and doubled
+ * centred coordinates u~ = 2u - (W-1), v~ = 2v - (H-1): count, sum u~^i v~^j (i + j <= 4),
+ * sum q u~^i v~^j (i + j <= 2) and sum q^2, in that order (i outer, j inner), each a signed
+ * 128-bit integer written as (low 64 bits, high 64 bits): sums is int64 [46] (device).
+ * W, H <= 4096. */
+pd_status pd_moments(pd_ctx* ctx, const float* D1, int W, int H, int64_t* sums);
+
+/* Eqs. (11)-(13): fits the road model of the given order (roll by minimising Eq. (12): closed form
+ * for order 1, 0.01-degree grid over +-15 degrees refined by golden-section search for order 2;
+ * coefficients by Eq. (11)), then D2 = max(0, D1 - f + delta_dt) in single precision, with
+ * delta_dt at invalid pixels.  The fit stays on the device (no host round trip).
+ * fitted: one pd_road_model (device, may be NULL); D2: float [H][W].  W, H <= 4096. */
+pd_status pd_transform(pd_ctx* ctx, const float* D1, int W, int H, int order, float delta_dt,
+                       pd_road_model* fitted, float* D2);
+
+/* ---------------------------------------------------------------- Sec. II-D: superpixels */
+
+/* SLIC on D2: grid interval S = sqrt(W H / K), nx = round(W / S), ny = round(H / S) seeds moved
+ * to the lowest-gradient pixel of their 3x3 neighbourhood; `iters` rounds of assignment (each
+ * pixel to the nearest centre whose 2S x 2S window covers it, distance
+ * (D2 - value)^2 + ((x - cx)^2 + (y - cy)^2) (m / S)^2, lower index on ties) and mean update.
+ * Then D3 (Sec. II-E): every pixel gets the mean D2 of its superpixel.
+ * labels: int32 [H][W]; D3: float [H][W]; centres (may be NULL): float [nx*ny][3].
+ * Returns the centre count in *n_centres (host, may be NULL). */
+pd_status pd_superpixels(pd_ctx* ctx, const float* D2, int W, int H, int K, float m, int iters,
+                         int32_t* labels, float* D3, float* centres, int* n_centres);
+
+/* ---------------------------------------------------------- Sec. II-E: pothole detection */
+
+/* Eqs. (14)-(17): the vectors g = [D2(p), sum of D2 over the 8 neighbours] of interior pixels
+ * whose 3x3 window is valid in D1 are split at thresholds t = k/8 px (k = 1..255) along the
+ * histogram diagonal; t_r minimises E2 (Eq. (17)); t_s = (mean D2 of the road cluster) - delta_pd
+ * (mode 0) or t_r - delta_pd (mode 1); mask = D3 < t_s.
+ * D2, D1, D3: float [H][W]; mask: uint8 [H][W]; thresholds (may be NULL): double [2] = t_r, t_s
+ * (device); E2 (may be NULL): double [256] (device, NaN where a cluster is empty). */
+pd_status pd_pothole_mask(pd_ctx* ctx, const float* D2, const float* D1, const float* D3, int W,
+                          int H, float delta_pd, int mode, uint8_t* mask, double* thresholds,
+                          double* E2);
+
+/* -------------------------------------------------------------------------- whole path */
+
+/* pd_sgm, pd_transform, pd_superpixels and pd_pothole_mask in sequence on one stream.
+ * times (host, may be NULL) receives per-stage device times (this synchronises the stream). */
+pd_status pd_run_pipeline(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H,
+                          size_t pitch, const pd_road_model* model, const pd_params* params,
+                          const pd_outputs* out, pd_stage_times* times);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
