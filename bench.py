@@ -1,0 +1,321 @@
+"""Benchmark: stereo pothole-detection path at 1280x720, D = 128, 8 paths on one GB300 per rank.
+
+A step is one pass of the whole path over one synthetic stereo pair: perspective warp, census
+cost, 8-path aggregation, winner-take-all / sub-pixel / left-right check, disparity
+transformation, SLIC and the adaptive threshold with the pothole mask.  The metric is disparity
+throughput W*H*D per second (Mdisp/s) over the whole step.  Inputs are resident in HBM; L2 is
+flushed (256 MiB write) before every timed step.  Prints one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+W_, H_, D_, PATHS_ = 1280, 720, 128, 8
+WORKLOAD = "road_1280x720_d128_8paths: warp+SGM+transform+SLIC(1000,10,10)+threshold+mask"
+METRIC = "SGM Mdisp/s (W*H*D/s) at 1280x720 D=128, 8 paths, whole path per step"
+# Aggregation: the recurrence needs 5 u16 lane-ops per (pixel, disparity, path) in the packed DPX
+# form (3-input min, add-min, add cost, running min, normalise); peak = 64 int instructions per
+# clock per SM (measured) x 2 u16 lanes x 152 SMs x max SM clock.
+AGG_LANE_OPS = 5
+INT_INSTR_PER_CLK_SM = 64
+SMS = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+class Clocks:
+    """Samples SM clock and throttle reasons with nvidia-smi while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", "-i", str(self.index),
+               "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+               "--format=csv,noheader,nounits", "-lms", "200"]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def agg_traffic_record():
+    """DRAM bytes per launch of the aggregation kernel from the committed ncu summary, if the
+    kernel source is unchanged since the counters were taken."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "aggregate_traffic.json")))
+        src = open(os.path.join(ROOT, "paper_2012_10802_gb300", "csrc", "sgm.cu"), "rb").read()
+        if rec.get("sgm_cu_sha256") == hashlib.sha256(src).hexdigest():
+            return rec.get("dram_bytes_per_launch_full")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def oracle_pipeline_time(left, right, model_tuple, rows):
+    """Times the oracle's whole path on a band of `rows` rows (single thread)."""
+    import oracle
+    p = oracle.Params(D=D_, paths=PATHS_, slic_K=max(1, round(1000 * rows / H_)))
+    m = oracle.RoadModel.make(*model_tuple)
+    t0 = time.perf_counter()
+    oracle.pipeline(left[:rows].copy(), right[:rows].copy(), m, p)
+    return time.perf_counter() - t0
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import numpy as np
+    from paper_2012_10802_gb300 import synth
+    import oracle
+    oracle.lib()
+    sc = synth.road_1280x720()
+    left, right = synth.render(sc)
+    rows = 72
+    for _ in range(args.warmup):
+        oracle_pipeline_time(left, right, synth.true_model(sc), rows)
+    ts = [oracle_pipeline_time(left, right, synth.true_model(sc), rows) for _ in range(args.steps)]
+    total = sum(ts)
+    val = args.steps * W_ * rows * D_ / total / 1e6
+    sample = "per step: a 1280x72 band (1/10 of the 720p frame), D=128, 8 paths, whole oracle path"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "Mdisp/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16+f32",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": val, "unit": "Mdisp/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": "Mdisp/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    from paper_2012_10802_gb300 import binding as B
+    from paper_2012_10802_gb300 import synth
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", rank=rank, world_size=world)
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # inputs: one synthetic pair per rank (independent frames: weak scaling, no collective)
+    sc = synth.road_1280x720(seed=2 + rank)
+    left_np, right_np = synth.render(sc)
+    model = B.RoadModel.make(*synth.true_model(sc))
+    params = B.default_params()
+    ctx = B.Context(local)
+    left = torch.from_numpy(left_np).cuda()
+    right = torch.from_numpy(right_np).cuda()
+    outs = B.make_outputs(ctx, W_, H_)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    for _ in range(max(args.warmup, 3)):
+        B.pd_run_pipeline(ctx, left, right, model, params, outs)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device time of K steps, L2 flushed before each step
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    B.pd_profile_enable(ctx, True)
+    with Clocks(local) as clk:
+        barrier()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(i & 0xff)
+            ev[i][0].record()
+            B.pd_run_pipeline(ctx, left, right, model, params, outs)
+            ev[i][1].record()
+        barrier()
+        wall = time.perf_counter() - t0
+    prof = B.pd_profile_read(ctx)
+    B.pd_profile_enable(ctx, False)
+    dev_ms = sum(a.elapsed_time(b) for a, b in ev)
+    t_max = dev_ms
+    if dist:
+        t = torch.tensor([dev_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = args.steps * world * W_ * H_ * D_ / (t_max * 1e-3) / 1e6
+
+    # ---- end to end through the public API: pinned host inputs in, the mask back out
+    e2e = None
+    if not args.no_e2e:
+        lh = torch.from_numpy(left_np).pin_memory()
+        rh = torch.from_numpy(right_np).pin_memory()
+        mh = torch.empty((H_, W_), dtype=torch.uint8).pin_memory()
+        ld, rd = torch.empty_like(left), torch.empty_like(right)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(2):
+            ld.copy_(lh, non_blocking=True)
+            rd.copy_(rh, non_blocking=True)
+            B.pd_run_pipeline(ctx, ld, rd, model, params, outs)
+            mh.copy_(outs[1]["mask"], non_blocking=True)
+        barrier()
+        e0.record()
+        for _ in range(args.steps):
+            ld.copy_(lh, non_blocking=True)
+            rd.copy_(rh, non_blocking=True)
+            B.pd_run_pipeline(ctx, ld, rd, model, params, outs)
+            mh.copy_(outs[1]["mask"], non_blocking=True)
+        e1.record()
+        barrier()
+        e2e_ms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([e2e_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": args.steps * world * W_ * H_ * D_ / (e2e_ms * 1e-3) / 1e6,
+               "unit": "Mdisp/s", "h2d_bytes_per_step": 2 * W_ * H_,
+               "d2h_bytes_per_step": W_ * H_, "ms_per_step": e2e_ms / args.steps}
+
+    if rank != 0:
+        ctx.close()
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    clocks = clk.summary()
+    peaks = measured_peaks()
+    calls = max(prof["calls"], 1)
+    agg_ms = prof["aggregate_ms"] / calls
+    sgm_ms = (prof["prep_ms"] + prof["aggregate_ms"] + prof["disparity_ms"]) / calls
+    units = W_ * H_ * D_ * PATHS_
+    sm_max = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    peak_lane_ops = INT_INSTR_PER_CLK_SM * 2 * SMS * sm_max * 1e6
+    achieved = AGG_LANE_OPS * units / (agg_ms * 1e-3)
+    traffic = agg_traffic_record()
+    roofline = {"kernel": "k_aggregate (Eq. 8, 8 directions, one launch)", "bound": "alu",
+                "achieved": achieved / 1e12, "peak": peak_lane_ops / 1e12,
+                "unit": "T u16-lane-ops/s", "frac": achieved / peak_lane_ops,
+                "traffic": traffic, "avg_launch_ms": agg_ms,
+                "hbm_view": {"bytes_per_launch": 2 * units,
+                             "achieved_GBs": 2 * units / (agg_ms * 1e-3) / 1e9,
+                             "peak_GBs": peaks.get("hbm_gbs"),
+                             "frac": (2 * units / (agg_ms * 1e-3) / 1e9) / peaks["hbm_gbs"]
+                             if peaks.get("hbm_gbs") else None},
+                "peak_source": "64 int instr/clk/SM (microbenchmark) x 2 lanes x 152 SMs x %.0f MHz" % sm_max}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.lib()
+        rows = 720
+        t_cpu = oracle_pipeline_time(left_np, right_np, synth.true_model(sc), rows)
+        cpu = {"value": W_ * rows * D_ / t_cpu / 1e6, "unit": "Mdisp/s", "cores": 1,
+               "kind": "oracle", "sample": "one full 1280x720 frame, whole oracle path, %.1f s" % t_cpu}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "Mdisp/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u16+f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "W": W_, "H": H_, "D": D_, "paths": PATHS_,
+                   "l2": "flushed before each timed step (256 MiB write)",
+                   "frames_per_s": args.steps * world / (t_max * 1e-3),
+                   "sgm_only_ms": sgm_ms, "sgm_only_Mdisp_s": W_ * H_ * D_ / (sgm_ms * 1e-3) / 1e6,
+                   "stage_ms": {k: prof[k] / calls for k in ("prep_ms", "aggregate_ms",
+                                                            "disparity_ms", "transform_ms",
+                                                            "superpixel_ms", "mask_ms")},
+                   "wall_s": wall},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": prof["launches"], "clocks": clocks,
+    }
+    print(json.dumps(out))
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -56,7 +56,7 @@ typedef struct {
 
 /* Method parameters.  pd_default_params() fills the defaults given in brackets. */
 typedef struct {
-  int D;              /* disparity range searched after the warp [128]; multiple of 32, 32..256 */
+  int D;              /* disparity range searched after the warp [128]: 32, 64, 128 or 256 */
   int paths;          /* aggregation directions, 4 or 8 [8] */
   int P1, P2;         /* Eq. (7)-(8) penalties lambda1 < lambda2 [4, 32]; 24 + P2 <= 255 */
   int lr_tol;         /* left-right consistency tolerance in pixels [1] */
@@ -88,6 +88,21 @@ typedef struct {
 typedef struct {
   float sgm_ms, transform_ms, superpixel_ms, mask_ms, total_ms;
 } pd_stage_times;
+
+/* Device times summed over the calls made while profiling was on (host struct, milliseconds).
+ * Stages a call does not run stay 0. */
+typedef struct {
+  int calls;            /* pd_sgm / pd_run_pipeline calls profiled */
+  int pad;
+  long long launches;   /* kernels those calls launched */
+  double prep_ms;       /* row shifts, census and matching cost */
+  double aggregate_ms;  /* Eq. (8) aggregation kernel */
+  double disparity_ms;  /* winner-take-all, right view, left-right check */
+  double transform_ms;  /* Sec. II-C */
+  double superpixel_ms; /* Sec. II-D and D3 */
+  double mask_ms;       /* Sec. II-E threshold and mask */
+  double total_ms;      /* first to last event of each call */
+} pd_profile;
 
 /* ------------------------------------------------------------------------------ context */
 
@@ -137,7 +152,8 @@ pd_status pd_cost(pd_ctx* ctx, const uint8_t* left, const uint8_t* right_warped,
  *   L(p, d) = c(p, d) + min(L(p-r, d), L(p-r, d-1) + P1, L(p-r, d+1) + P1, m + P2) - m,
  *   m = min_i L(p-r, i), and L = c where p - r is outside the image.
  * Subtracting m (the printed equation omits it) changes every d of a pixel by the same amount.
- * cost: uint8 [H][W][D]; L: uint8 [H][W][D].  D multiple of 32, 32..256. */
+ * cost: uint8 [H][W][D]; L: uint8 [H][W][D].  D in {32, 64, 128, 256}; cost and L 16-byte
+ * aligned. */
 pd_status pd_aggregate_dir(pd_ctx* ctx, const uint8_t* cost, int W, int H, int D, int dx, int dy,
                            int P1, int P2, uint8_t* L);
 
@@ -206,6 +222,16 @@ pd_status pd_superpixels(pd_ctx* ctx, const float* D2, int W, int H, int K, floa
 pd_status pd_pothole_mask(pd_ctx* ctx, const float* D2, const float* D1, const float* D3, int W,
                           int H, float delta_pd, int mode, uint8_t* mask, double* thresholds,
                           double* E2);
+
+/* --------------------------------------------------------------------------- profiling */
+
+/* on != 0: later pd_sgm and pd_run_pipeline calls record CUDA events on the context's stream
+ * around their stages (no synchronisation; at most 4096 calls are recorded between reads).
+ * on == 0 stops recording and discards what was recorded. */
+pd_status pd_profile_enable(pd_ctx* ctx, int on);
+/* Waits for the recorded events, writes the summed stage times to *out (host) and starts a new
+ * recording. */
+pd_status pd_profile_read(pd_ctx* ctx, pd_profile* out);
 
 /* -------------------------------------------------------------------------- whole path */
 

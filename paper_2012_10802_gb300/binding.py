@@ -1,0 +1,327 @@
+"""Thin Python binding of libpothole's C ABI (include/pothole.h), with the same call names.
+
+Argument marshalling only: tensors are passed as device pointers with their sizes, outputs are
+allocated with torch when not given, and every computation runs in the library's CUDA kernels.
+There is no CPU fallback: if the library is missing or no GPU is present, calls raise.
+"""
+import ctypes as C
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libpothole.so")
+
+PD_OK, PD_ERR_INVALID_ARG, PD_ERR_OOM, PD_ERR_CUDA, PD_ERR_TIMEOUT, PD_ERR_UNSUPPORTED = range(6)
+STATUS_NAMES = {0: "PD_OK", 1: "PD_ERR_INVALID_ARG", 2: "PD_ERR_OOM", 3: "PD_ERR_CUDA",
+                4: "PD_ERR_TIMEOUT", 5: "PD_ERR_UNSUPPORTED"}
+
+
+class PdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class RoadModel(C.Structure):
+    _fields_ = [("order", C.c_int), ("a", C.c_double * 3), ("roll", C.c_double)]
+
+    @staticmethod
+    def make(order, a, roll):
+        m = RoadModel()
+        m.order = int(order)
+        for i in range(3):
+            m.a[i] = float(a[i]) if i < len(a) else 0.0
+        m.roll = float(roll)
+        return m
+
+    @staticmethod
+    def from_tensor(t):
+        """Reads one pd_road_model from a uint8 tensor of its bytes (e.g. a device output)."""
+        raw = bytes(t.detach().to("cpu").contiguous().numpy().tobytes())
+        return RoadModel.from_buffer_copy(raw[:C.sizeof(RoadModel)])
+
+
+class Params(C.Structure):
+    _fields_ = [("D", C.c_int), ("paths", C.c_int), ("P1", C.c_int), ("P2", C.c_int),
+                ("lr_tol", C.c_int), ("delta_pt", C.c_float), ("delta_dt", C.c_float),
+                ("delta_pd", C.c_float), ("slic_K", C.c_int), ("slic_m", C.c_float),
+                ("slic_iters", C.c_int), ("model_order", C.c_int), ("threshold_mode", C.c_int)]
+
+
+class Outputs(C.Structure):
+    _fields_ = [("kappa", C.c_void_p), ("d_int", C.c_void_p), ("D1", C.c_void_p),
+                ("fitted", C.c_void_p), ("D2", C.c_void_p), ("labels", C.c_void_p),
+                ("D3", C.c_void_p), ("thresholds", C.c_void_p), ("mask", C.c_void_p)]
+
+
+class StageTimes(C.Structure):
+    _fields_ = [("sgm_ms", C.c_float), ("transform_ms", C.c_float),
+                ("superpixel_ms", C.c_float), ("mask_ms", C.c_float), ("total_ms", C.c_float)]
+
+
+class Profile(C.Structure):
+    _fields_ = [("calls", C.c_int), ("pad", C.c_int), ("launches", C.c_longlong),
+                ("prep_ms", C.c_double), ("aggregate_ms", C.c_double),
+                ("disparity_ms", C.c_double), ("transform_ms", C.c_double),
+                ("superpixel_ms", C.c_double), ("mask_ms", C.c_double), ("total_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+_P, _i, _z, _f = C.c_void_p, C.c_int, C.c_size_t, C.c_float
+SIGNATURES = {
+    "pd_create": [C.POINTER(C.c_void_p), _i, _P],
+    "pd_destroy": [_P],
+    "pd_set_stream": [_P, _P],
+    "pd_default_params": [C.POINTER(Params)],
+    "pd_warp": [_P, _P, _i, _i, _z, C.POINTER(RoadModel), _f, _P, _P],
+    "pd_census": [_P, _P, _i, _i, _z, _P],
+    "pd_cost": [_P, _P, _P, _i, _i, _z, _i, _P],
+    "pd_aggregate_dir": [_P, _P, _i, _i, _i, _i, _i, _i, _i, _P],
+    "pd_aggregate": [_P, _P, _i, _i, _i, _i, _i, _i, _P],
+    "pd_disparity": [_P, _P, _i, _i, _i, _P, _i, _P, _P],
+    "pd_sgm": [_P, _P, _P, _i, _i, _z, C.POINTER(RoadModel), C.POINTER(Params), _P, _P, _P],
+    "pd_moments": [_P, _P, _i, _i, _P],
+    "pd_transform": [_P, _P, _i, _i, _i, _f, _P, _P],
+    "pd_superpixels": [_P, _P, _i, _i, _i, _f, _i, _P, _P, _P, C.POINTER(_i)],
+    "pd_pothole_mask": [_P, _P, _P, _P, _i, _i, _f, _i, _P, _P, _P],
+    "pd_run_pipeline": [_P, _P, _P, _i, _i, _z, C.POINTER(RoadModel), C.POINTER(Params),
+                        C.POINTER(Outputs), C.POINTER(StageTimes)],
+    "pd_profile_enable": [_P, _i],
+    "pd_profile_read": [_P, C.POINTER(Profile)],
+}
+EXTRA = {"pd_last_error": (C.c_char_p, [_P]), "pd_workspace_bytes": (C.c_size_t, [_P])}
+
+_lib = None
+
+
+def lib():
+    """Loads libpothole.so (built by __graft_entry__.build()); raises if it is absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libpothole.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        for name, args in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = C.c_int
+            fn.argtypes = args
+        for name, (res, args) in EXTRA.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def default_params(**overrides):
+    p = Params()
+    lib().pd_default_params(C.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """Owns one pd_ctx bound to a device and a stream (torch's current stream by default)."""
+
+    def __init__(self, device=0, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libpothole needs a CUDA GPU; none is available")
+        self.device = torch.device("cuda", device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        h = C.c_void_p()
+        st = lib().pd_create(C.byref(h), device, C.c_void_p(stream.cuda_stream))
+        if st != PD_OK:
+            raise PdError(st, "pd_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self.stream = stream
+        self.check(lib().pd_set_stream(self.h, C.c_void_p(stream.cuda_stream)))
+
+    def last_error(self):
+        return lib().pd_last_error(self.h).decode()
+
+    def workspace_bytes(self):
+        return int(lib().pd_workspace_bytes(self.h))
+
+    def check(self, st):
+        if st != PD_OK:
+            raise PdError(st, self.last_error())
+
+    def empty(self, shape, dtype):
+        return torch.empty(shape, dtype=dtype, device=self.device)
+
+
+# ------------------------------------------------------------------ calls, C-ABI names
+
+def pd_warp(ctx, right, model, delta_pt, right_warped=None, kappa=None, want_image=True):
+    H, W = right.shape
+    if kappa is None:
+        kappa = ctx.empty((H,), torch.int32)
+    if want_image and right_warped is None:
+        right_warped = ctx.empty((H, W), torch.uint8)
+    ctx.check(lib().pd_warp(ctx.h, _ptr(right), W, H, W, C.byref(model), float(delta_pt),
+                            _ptr(right_warped) if want_image else None, _ptr(kappa)))
+    return right_warped, kappa
+
+
+def pd_census(ctx, img, codes=None):
+    H, W = img.shape
+    if codes is None:
+        codes = ctx.empty((H, W), torch.int32)
+    ctx.check(lib().pd_census(ctx.h, _ptr(img), W, H, W, _ptr(codes)))
+    return codes
+
+
+def pd_cost(ctx, left, right_warped, D, cost=None):
+    H, W = left.shape
+    if cost is None:
+        cost = ctx.empty((H, W, D), torch.uint8)
+    ctx.check(lib().pd_cost(ctx.h, _ptr(left), _ptr(right_warped), W, H, W, D, _ptr(cost)))
+    return cost
+
+
+def pd_aggregate_dir(ctx, cost, dx, dy, P1, P2, L=None):
+    H, W, D = cost.shape
+    if L is None:
+        L = ctx.empty((H, W, D), torch.uint8)
+    ctx.check(lib().pd_aggregate_dir(ctx.h, _ptr(cost), W, H, D, dx, dy, P1, P2, _ptr(L)))
+    return L
+
+
+def pd_aggregate(ctx, cost, paths, P1, P2, S=None):
+    H, W, D = cost.shape
+    if S is None:
+        S = ctx.empty((H, W, D), torch.int16)
+    ctx.check(lib().pd_aggregate(ctx.h, _ptr(cost), W, H, D, paths, P1, P2, _ptr(S)))
+    return S
+
+
+def pd_disparity(ctx, S, kappa, lr_tol, d_int=None, D1=None):
+    H, W, D = S.shape
+    if d_int is None:
+        d_int = ctx.empty((H, W), torch.int16)
+    if D1 is None:
+        D1 = ctx.empty((H, W), torch.float32)
+    ctx.check(lib().pd_disparity(ctx.h, _ptr(S), W, H, D, _ptr(kappa), lr_tol, _ptr(d_int),
+                                 _ptr(D1)))
+    return d_int, D1
+
+
+def pd_sgm(ctx, left, right, model, params, kappa=None, d_int=None, D1=None):
+    H, W = left.shape
+    if kappa is None:
+        kappa = ctx.empty((H,), torch.int32)
+    if d_int is None:
+        d_int = ctx.empty((H, W), torch.int16)
+    if D1 is None:
+        D1 = ctx.empty((H, W), torch.float32)
+    ctx.check(lib().pd_sgm(ctx.h, _ptr(left), _ptr(right), W, H, W, C.byref(model),
+                           C.byref(params), _ptr(kappa), _ptr(d_int), _ptr(D1)))
+    return kappa, d_int, D1
+
+
+def pd_moments(ctx, D1, sums=None):
+    H, W = D1.shape
+    if sums is None:
+        sums = ctx.empty((46,), torch.int64)
+    ctx.check(lib().pd_moments(ctx.h, _ptr(D1), W, H, _ptr(sums)))
+    return sums
+
+
+def pd_transform(ctx, D1, order, delta_dt, fitted=None, D2=None):
+    H, W = D1.shape
+    if fitted is None:
+        fitted = ctx.empty((C.sizeof(RoadModel),), torch.uint8)
+    if D2 is None:
+        D2 = ctx.empty((H, W), torch.float32)
+    ctx.check(lib().pd_transform(ctx.h, _ptr(D1), W, H, order, float(delta_dt), _ptr(fitted),
+                                 _ptr(D2)))
+    return fitted, D2
+
+
+def pd_superpixels(ctx, D2, K, m, iters, labels=None, D3=None, want_centres=False):
+    H, W = D2.shape
+    if labels is None:
+        labels = ctx.empty((H, W), torch.int32)
+    if D3 is None:
+        D3 = ctx.empty((H, W), torch.float32)
+    n = C.c_int(0)
+    centres = ctx.empty((W * H * 3,), torch.float32) if want_centres else None
+    ctx.check(lib().pd_superpixels(ctx.h, _ptr(D2), W, H, K, float(m), iters, _ptr(labels),
+                                   _ptr(D3), _ptr(centres), C.byref(n)))
+    if want_centres:
+        centres = centres[:3 * n.value].view(n.value, 3)
+    return labels, D3, centres, n.value
+
+
+def pd_pothole_mask(ctx, D2, D1, D3, delta_pd, mode=0, mask=None, thresholds=None, E2=None):
+    H, W = D2.shape
+    if mask is None:
+        mask = ctx.empty((H, W), torch.uint8)
+    if thresholds is None:
+        thresholds = ctx.empty((2,), torch.float64)
+    ctx.check(lib().pd_pothole_mask(ctx.h, _ptr(D2), _ptr(D1), _ptr(D3), W, H, float(delta_pd),
+                                    mode, _ptr(mask), _ptr(thresholds), _ptr(E2)))
+    return mask, thresholds
+
+
+def make_outputs(ctx, W, H):
+    """Allocates every pd_outputs buffer for a W x H frame; returns (Outputs, dict of tensors)."""
+    t = {"kappa": ctx.empty((H,), torch.int32), "d_int": ctx.empty((H, W), torch.int16),
+         "D1": ctx.empty((H, W), torch.float32),
+         "fitted": ctx.empty((C.sizeof(RoadModel),), torch.uint8),
+         "D2": ctx.empty((H, W), torch.float32), "labels": ctx.empty((H, W), torch.int32),
+         "D3": ctx.empty((H, W), torch.float32), "thresholds": ctx.empty((2,), torch.float64),
+         "mask": ctx.empty((H, W), torch.uint8)}
+    o = Outputs()
+    for k, v in t.items():
+        setattr(o, k, v.data_ptr())
+    return o, t
+
+
+def pd_run_pipeline(ctx, left, right, model, params, outputs, times=False):
+    H, W = left.shape
+    o, _ = outputs
+    st = StageTimes() if times else None
+    ctx.check(lib().pd_run_pipeline(ctx.h, _ptr(left), _ptr(right), W, H, W, C.byref(model),
+                                    C.byref(params), C.byref(o),
+                                    C.byref(st) if times else None))
+    return st
+
+
+def pd_profile_enable(ctx, on=True):
+    ctx.check(lib().pd_profile_enable(ctx.h, 1 if on else 0))
+
+
+def pd_profile_read(ctx):
+    p = Profile()
+    ctx.check(lib().pd_profile_read(ctx.h, C.byref(p)))
+    return p.as_dict()

@@ -1,0 +1,566 @@
+// The C ABI of libpothole (declared in include/pothole.h): argument validation, scratch
+// management and the launch sequences of each stage.  Every computation runs in the kernels of
+// sgm.cu, dt.cu and detect.cu.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "common.cuh"
+
+namespace pd {
+
+pd_status fail(pd_ctx* c, pd_status st, const char* fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+  }
+  return st;
+}
+
+pd_status cuda_ok(pd_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return PD_OK;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(c, PD_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  }
+  return fail(c, PD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+pd_status launched(pd_ctx* c, const char* what) { return cuda_ok(c, cudaGetLastError(), what); }
+
+pd_status ensure_ws(pd_ctx* c, size_t bytes) {
+  if (bytes <= c->ws_bytes) return PD_OK;
+  if (c->ws) {
+    cudaFree(c->ws);  // synchronises the device, so no kernel still uses the old scratch
+    c->ws = nullptr;
+    c->ws_bytes = 0;
+  }
+  size_t want = bytes + (bytes >> 4);
+  cudaError_t e = cudaMalloc(&c->ws, want);
+  if (e != cudaSuccess) {
+    c->ws = nullptr;
+    cudaGetLastError();
+    return fail(c, PD_ERR_OOM, "scratch of %zu bytes: %s", want, cudaGetErrorString(e));
+  }
+  c->ws_bytes = want;
+  return PD_OK;
+}
+
+}  // namespace pd
+
+using namespace pd;
+
+namespace {
+
+#define PD_TRY(x)                   \
+  do {                              \
+    pd_status _st = (x);            \
+    if (_st != PD_OK) return _st;   \
+  } while (0)
+
+#define PD_REQUIRE(cond, ...)                                          \
+  do {                                                                 \
+    if (!(cond)) return fail(ctx, PD_ERR_INVALID_ARG, __VA_ARGS__);    \
+  } while (0)
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// ---------------------------------------------------------------- profiling marks
+constexpr int kMaxProf = 4096;
+
+pd_prof_rec* prof_begin(pd_ctx* c) {
+  if (!c->prof) return nullptr;
+  if (!c->recs) c->recs = new pd_prof_rec[kMaxProf]();
+  if (c->nrec >= kMaxProf) return nullptr;
+  pd_prof_rec* r = &c->recs[c->nrec++];
+  r->used = 0;
+  return r;
+}
+
+void mark(pd_ctx* c, pd_prof_rec* r, int i) {
+  if (!r) return;
+  if (!r->ev[i] && cudaEventCreate(&r->ev[i]) != cudaSuccess) {
+    cudaGetLastError();
+    r->ev[i] = nullptr;
+    return;
+  }
+  cudaEventRecord(r->ev[i], c->stream);
+  r->used |= 1 << i;
+}
+
+void count_launches(pd_ctx* c, int n) {
+  if (c->prof) c->launches += n;
+}
+bool pow2_d(int D) { return D == 32 || D == 64 || D == 128 || D == 256; }
+
+pd_status begin(pd_ctx* ctx) {
+  if (!ctx) return PD_ERR_INVALID_ARG;
+  ctx->err[0] = 0;
+  return cuda_ok(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+}
+
+pd_status check_image(pd_ctx* ctx, int W, int H, size_t pitch) {
+  PD_REQUIRE(W >= 1 && H >= 1, "image size %dx%d must be positive", W, H);
+  PD_REQUIRE(W <= 16384 && H <= 16384, "image size %dx%d exceeds 16384", W, H);
+  PD_REQUIRE(pitch >= (size_t)W, "pitch %zu is smaller than the width %d", pitch, W);
+  return PD_OK;
+}
+
+pd_status check_model(pd_ctx* ctx, const pd_road_model* m) {
+  PD_REQUIRE(m != nullptr, "road model is NULL");
+  PD_REQUIRE(m->order == 1 || m->order == 2, "road model order %d must be 1 or 2", m->order);
+  PD_REQUIRE(isfinite(m->a[0]) && isfinite(m->a[1]) && isfinite(m->a[2]) && isfinite(m->roll),
+             "road model has a non-finite coefficient");
+  return PD_OK;
+}
+
+pd_status check_penalties(pd_ctx* ctx, int P1, int P2) {
+  PD_REQUIRE(P1 >= 0 && P1 < P2, "penalties must satisfy 0 <= P1 < P2 (got %d, %d)", P1, P2);
+  PD_REQUIRE(kCensusBits + P2 <= 255, "P2 = %d too large: 24 + P2 must fit in a byte", P2);
+  return PD_OK;
+}
+
+// Scratch layout of the fused SGM path.
+struct SgmScratch {
+  uint32_t* cl;
+  uint32_t* cr;
+  uint8_t* cost;
+  uint8_t* vols;
+  float* dsub;
+  uint32_t* rkeys;
+  int32_t* kappa;
+};
+
+size_t sgm_scratch_bytes(int W, int H, int D, int paths) {
+  size_t N = (size_t)W * H, acc = 0;
+  carve_size<uint32_t>(acc, N);
+  carve_size<uint32_t>(acc, N);
+  carve_size<uint8_t>(acc, N * D);
+  carve_size<uint8_t>(acc, N * D * paths);
+  carve_size<float>(acc, N);
+  carve_size<uint32_t>(acc, N);
+  carve_size<int32_t>(acc, H);
+  return acc;
+}
+
+SgmScratch sgm_carve(void* base, int W, int H, int D, int paths) {
+  size_t N = (size_t)W * H;
+  Carve c(base);
+  SgmScratch s;
+  s.cl = c.take<uint32_t>(N);
+  s.cr = c.take<uint32_t>(N);
+  s.cost = c.take<uint8_t>(N * D);
+  s.vols = c.take<uint8_t>(N * D * paths);
+  s.dsub = c.take<float>(N);
+  s.rkeys = c.take<uint32_t>(N);
+  s.kappa = c.take<int32_t>(H);
+  return s;
+}
+
+pd_status check_sgm_params(pd_ctx* ctx, const pd_params* p) {
+  PD_REQUIRE(p != nullptr, "params is NULL");
+  PD_REQUIRE(pow2_d(p->D), "D = %d must be 32, 64, 128 or 256", p->D);
+  PD_REQUIRE(p->paths == 4 || p->paths == 8, "paths = %d must be 4 or 8", p->paths);
+  PD_TRY(check_penalties(ctx, p->P1, p->P2));
+  PD_REQUIRE(p->lr_tol >= 0, "lr_tol = %d must be >= 0", p->lr_tol);
+  PD_REQUIRE(isfinite(p->delta_pt), "delta_pt must be finite");
+  return PD_OK;
+}
+
+// Enqueues the fused SGM (no validation; scratch already sized).
+pd_status sgm_enqueue(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H,
+                      size_t pitch, const pd_road_model* model, const pd_params* p,
+                      int32_t* kappa, int16_t* d_int, float* D1, pd_prof_rec* rec) {
+  cudaStream_t s = ctx->stream;
+  SgmScratch sc = sgm_carve(ctx->ws, W, H, p->D, p->paths);
+  int32_t* kap = kappa ? kappa : sc.kappa;
+  size_t N = (size_t)W * H;
+  size_t vol = N * p->D;
+  mark(ctx, rec, 0);
+  launch_kappa(s, W, H, model->order, model->a, cos(model->roll), sin(model->roll),
+               (double)p->delta_pt, kap);
+  launch_census(s, left, W, H, pitch, nullptr, sc.cl);
+  launch_census(s, right, W, H, pitch, kap, sc.cr);
+  launch_cost(s, sc.cl, sc.cr, W, H, p->D, 1, sc.cost);
+  cudaMemsetAsync(sc.rkeys, 0xff, N * sizeof(uint32_t), s);
+  mark(ctx, rec, 1);
+  launch_aggregate(s, sc.cost, W, H, p->D, dir_set(p->paths), p->P1, p->P2, sc.vols, vol);
+  mark(ctx, rec, 2);
+  launch_wta(s, sc.vols, p->paths, vol, nullptr, W, H, p->D, d_int, sc.dsub, sc.rkeys);
+  launch_lr(s, d_int, sc.dsub, sc.rkeys, kap, W, H, p->D, p->lr_tol, D1);
+  mark(ctx, rec, 3);
+  count_launches(ctx, 7);
+  return launched(ctx, "pd_sgm");
+}
+
+size_t transform_scratch_bytes(int W, int H) {
+  size_t acc = 0;
+  carve_size<uint8_t>(acc, moments_scratch_bytes(W, H));
+  carve_size<int64_t>(acc, 46);
+  carve_size<pd_road_model>(acc, 1);
+  carve_size<RoadCoefF>(acc, 1);
+  return acc;
+}
+
+pd_status transform_enqueue(pd_ctx* ctx, const float* D1, int W, int H, int order,
+                            float delta_dt, pd_road_model* fitted, float* D2, void* base) {
+  Carve c(base);
+  void* part = c.take<uint8_t>(moments_scratch_bytes(W, H));
+  int64_t* sums = c.take<int64_t>(46);
+  pd_road_model* fit = c.take<pd_road_model>(1);
+  RoadCoefF* coef = c.take<RoadCoefF>(1);
+  cudaStream_t s = ctx->stream;
+  launch_moments(s, D1, W, H, part, sums);
+  launch_roll_solve(s, sums, order, W, H, fitted ? fitted : fit, coef);
+  launch_d2(s, D1, W, H, coef, delta_dt, D2);
+  count_launches(ctx, 4);
+  return launched(ctx, "pd_transform");
+}
+
+}  // namespace
+
+// ============================================================================== C ABI
+
+extern "C" {
+
+pd_status pd_create(pd_ctx** out, int device, void* stream) {
+  if (!out) return PD_ERR_INVALID_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return PD_ERR_INVALID_ARG;
+  }
+  pd_ctx* c = new pd_ctx();
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return PD_ERR_CUDA;
+  }
+  *out = c;
+  return PD_OK;
+}
+
+pd_status pd_destroy(pd_ctx* ctx) {
+  if (!ctx) return PD_OK;
+  cudaSetDevice(ctx->device);
+  if (ctx->ws) cudaFree(ctx->ws);
+  for (auto& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->recs) {
+    for (int i = 0; i < kMaxProf; ++i)
+      for (auto& e : ctx->recs[i].ev)
+        if (e) cudaEventDestroy(e);
+    delete[] ctx->recs;
+  }
+  delete ctx;
+  return PD_OK;
+}
+
+pd_status pd_set_stream(pd_ctx* ctx, void* stream) {
+  if (!ctx) return PD_ERR_INVALID_ARG;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  return PD_OK;
+}
+
+const char* pd_last_error(const pd_ctx* ctx) { return ctx ? ctx->err : "context is NULL"; }
+
+size_t pd_workspace_bytes(const pd_ctx* ctx) { return ctx ? ctx->ws_bytes : 0; }
+
+pd_status pd_default_params(pd_params* p) {
+  if (!p) return PD_ERR_INVALID_ARG;
+  p->D = 128;
+  p->paths = 8;
+  p->P1 = 4;
+  p->P2 = 32;
+  p->lr_tol = 1;
+  p->delta_pt = 10.0f;
+  p->delta_dt = 16.0f;
+  p->delta_pd = 2.36f;
+  p->slic_K = 1000;
+  p->slic_m = 10.0f;
+  p->slic_iters = 10;
+  p->model_order = 2;
+  p->threshold_mode = 0;
+  return PD_OK;
+}
+
+pd_status pd_warp(pd_ctx* ctx, const uint8_t* right, int W, int H, size_t pitch,
+                  const pd_road_model* model, float delta_pt, uint8_t* right_warped,
+                  int32_t* kappa) {
+  PD_TRY(begin(ctx));
+  PD_TRY(check_image(ctx, W, H, pitch));
+  PD_TRY(check_model(ctx, model));
+  PD_REQUIRE(kappa != nullptr, "kappa is NULL");
+  PD_REQUIRE(right_warped == nullptr || right != nullptr, "right is NULL");
+  PD_REQUIRE(isfinite(delta_pt), "delta_pt must be finite");
+  launch_kappa(ctx->stream, W, H, model->order, model->a, cos(model->roll), sin(model->roll),
+               (double)delta_pt, kappa);
+  if (right_warped) launch_warp(ctx->stream, right, W, H, pitch, kappa, right_warped);
+  return launched(ctx, "pd_warp");
+}
+
+pd_status pd_census(pd_ctx* ctx, const uint8_t* img, int W, int H, size_t pitch,
+                    uint32_t* codes) {
+  PD_TRY(begin(ctx));
+  PD_TRY(check_image(ctx, W, H, pitch));
+  PD_REQUIRE(img && codes, "NULL image or output");
+  launch_census(ctx->stream, img, W, H, pitch, nullptr, codes);
+  return launched(ctx, "pd_census");
+}
+
+pd_status pd_cost(pd_ctx* ctx, const uint8_t* left, const uint8_t* right_warped, int W, int H,
+                  size_t pitch, int D, uint8_t* cost) {
+  PD_TRY(begin(ctx));
+  PD_TRY(check_image(ctx, W, H, pitch));
+  PD_REQUIRE(left && right_warped && cost, "NULL image or output");
+  PD_REQUIRE(D >= 1 && D <= kMaxD, "D = %d must be in 1..256", D);
+  size_t N = (size_t)W * H, need = 0;
+  carve_size<uint32_t>(need, N);
+  carve_size<uint32_t>(need, N);
+  PD_TRY(ensure_ws(ctx, need));
+  Carve c(ctx->ws);
+  uint32_t* cl = c.take<uint32_t>(N);
+  uint32_t* cr = c.take<uint32_t>(N);
+  launch_census(ctx->stream, left, W, H, pitch, nullptr, cl);
+  launch_census(ctx->stream, right_warped, W, H, pitch, nullptr, cr);
+  launch_cost(ctx->stream, cl, cr, W, H, D, 0, cost);
+  return launched(ctx, "pd_cost");
+}
+
+pd_status pd_aggregate_dir(pd_ctx* ctx, const uint8_t* cost, int W, int H, int D, int dx, int dy,
+                           int P1, int P2, uint8_t* L) {
+  PD_TRY(begin(ctx));
+  PD_TRY(check_image(ctx, W, H, (size_t)W));
+  PD_REQUIRE(cost && L, "NULL cost or output");
+  PD_REQUIRE(aligned16(cost) && aligned16(L), "cost and L must be 16-byte aligned");
+  PD_REQUIRE(pow2_d(D), "D = %d must be 32, 64, 128 or 256", D);
+  PD_REQUIRE(dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && (dx != 0 || dy != 0),
+             "direction (%d, %d) must have components in {-1, 0, 1}, not both 0", dx, dy);
+  PD_TRY(check_penalties(ctx, P1, P2));
+  size_t vol = (size_t)W * H * D, need = 0;
+  carve_size<uint8_t>(need, vol);
+  carve_size<uint8_t>(need, vol);
+  PD_TRY(ensure_ws(ctx, need));
+  Carve c(ctx->ws);
+  uint8_t* cil = c.take<uint8_t>(vol);
+  uint8_t* lil = c.take<uint8_t>(vol);
+  launch_to_interleaved(ctx->stream, cost, (size_t)W * H, D, cil);
+  launch_aggregate(ctx->stream, cil, W, H, D, one_dir(dx, dy), P1, P2, lil, vol);
+  launch_to_natural(ctx->stream, lil, (size_t)W * H, D, L);
+  return launched(ctx, "pd_aggregate_dir");
+}
+
+pd_status pd_aggregate(pd_ctx* ctx, const uint8_t* cost, int W, int H, int D, int paths, int P1,
+                       int P2, uint16_t* S) {
+  PD_TRY(begin(ctx));
+  PD_TRY(check_image(ctx, W, H, (size_t)W));
+  PD_REQUIRE(cost && S, "NULL cost or output");
+  PD_REQUIRE(aligned16(cost) && aligned16(S), "cost and S must be 16-byte aligned");
+  PD_REQUIRE(pow2_d(D), "D = %d must be 32, 64, 128 or 256", D);
+  PD_REQUIRE(paths == 4 || paths == 8, "paths = %d must be 4 or 8", paths);
+  PD_TRY(check_penalties(ctx, P1, P2));
+  size_t vol = (size_t)W * H * D, need = 0;
+  carve_size<uint8_t>(need, vol);
+  carve_size<uint8_t>(need, vol * paths);
+  PD_TRY(ensure_ws(ctx, need));
+  Carve c(ctx->ws);
+  uint8_t* cil = c.take<uint8_t>(vol);
+  uint8_t* vols = c.take<uint8_t>(vol * paths);
+  launch_to_interleaved(ctx->stream, cost, (size_t)W * H, D, cil);
+  launch_aggregate(ctx->stream, cil, W, H, D, dir_set(paths), P1, P2, vols, vol);
+  launch_sum_volumes(ctx->stream, vols, paths, vol, W, H, D, S);
+  return launched(ctx, "pd_aggregate");
+}
+
+pd_status pd_disparity(pd_ctx* ctx, const uint16_t* S, int W, int H, int D, const int32_t* kappa,
+                       int lr_tol, int16_t* d_int, float* D1) {
+  PD_TRY(begin(ctx));
+  PD_TRY(check_image(ctx, W, H, (size_t)W));
+  PD_REQUIRE(S && kappa && d_int && D1, "NULL input or output");
+  PD_REQUIRE(aligned16(S), "S must be 16-byte aligned");
+  PD_REQUIRE(pow2_d(D), "D = %d must be 32, 64, 128 or 256", D);
+  PD_REQUIRE(lr_tol >= 0, "lr_tol = %d must be >= 0", lr_tol);
+  size_t N = (size_t)W * H, need = 0;
+  carve_size<float>(need, N);
+  carve_size<uint32_t>(need, N);
+  PD_TRY(ensure_ws(ctx, need));
+  Carve c(ctx->ws);
+  float* dsub = c.take<float>(N);
+  uint32_t* rkeys = c.take<uint32_t>(N);
+  cudaMemsetAsync(rkeys, 0xff, N * sizeof(uint32_t), ctx->stream);
+  launch_wta(ctx->stream, nullptr, 0, 0, S, W, H, D, d_int, dsub, rkeys);
+  launch_lr(ctx->stream, d_int, dsub, rkeys, kappa, W, H, D, lr_tol, D1);
+  return launched(ctx, "pd_disparity");
+}
+
+pd_status pd_sgm(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H,
+                 size_t pitch, const pd_road_model* model, const pd_params* params,
+                 int32_t* kappa, int16_t* d_int, float* D1) {
+  PD_TRY(begin(ctx));
+  PD_TRY(check_image(ctx, W, H, pitch));
+  PD_TRY(check_model(ctx, model));
+  PD_TRY(check_sgm_params(ctx, params));
+  PD_REQUIRE(left && right && d_int && D1, "NULL input or output");
+  PD_TRY(ensure_ws(ctx, sgm_scratch_bytes(W, H, params->D, params->paths)));
+  return sgm_enqueue(ctx, left, right, W, H, pitch, model, params, kappa, d_int, D1,
+                     prof_begin(ctx));
+}
+
+pd_status pd_moments(pd_ctx* ctx, const float* D1, int W, int H, int64_t* sums) {
+  PD_TRY(begin(ctx));
+  PD_TRY(check_image(ctx, W, H, (size_t)W));
+  PD_REQUIRE(W <= kMaxImage && H <= kMaxImage, "moments need W, H <= %d", kMaxImage);
+  PD_REQUIRE(D1 && sums, "NULL input or output");
+  PD_TRY(ensure_ws(ctx, moments_scratch_bytes(W, H)));
+  launch_moments(ctx->stream, D1, W, H, ctx->ws, sums);
+  return launched(ctx, "pd_moments");
+}
+
+pd_status pd_transform(pd_ctx* ctx, const float* D1, int W, int H, int order, float delta_dt,
+                       pd_road_model* fitted, float* D2) {
+  PD_TRY(begin(ctx));
+  PD_TRY(check_image(ctx, W, H, (size_t)W));
+  PD_REQUIRE(W <= kMaxImage && H <= kMaxImage, "transform needs W, H <= %d", kMaxImage);
+  PD_REQUIRE(D1 && D2, "NULL input or output");
+  PD_REQUIRE(order == 1 || order == 2, "order %d must be 1 or 2", order);
+  PD_REQUIRE(isfinite(delta_dt), "delta_dt must be finite");
+  PD_TRY(ensure_ws(ctx, transform_scratch_bytes(W, H)));
+  return transform_enqueue(ctx, D1, W, H, order, delta_dt, fitted, D2, ctx->ws);
+}
+
+pd_status pd_superpixels(pd_ctx* ctx, const float* D2, int W, int H, int K, float m, int iters,
+                         int32_t* labels, float* D3, float* centres, int* n_centres) {
+  PD_TRY(begin(ctx));
+  PD_TRY(check_image(ctx, W, H, (size_t)W));
+  PD_REQUIRE(D2 && labels && D3, "NULL input or output");
+  PD_REQUIRE(K >= 1 && (size_t)K <= (size_t)W * H, "K = %d must be in 1..W*H", K);
+  PD_REQUIRE(isfinite(m) && m > 0.0f, "compactness m must be positive");
+  PD_REQUIRE(iters >= 0 && iters <= 1000, "iters = %d must be in 0..1000", iters);
+  int nx, ny;
+  slic_grid(W, H, K, &nx, &ny);
+  if (n_centres) *n_centres = nx * ny;
+  PD_TRY(ensure_ws(ctx, slic_scratch_bytes(nx * ny)));
+  launch_slic(ctx->stream, D2, W, H, K, m, iters, labels, D3, centres, ctx->ws);
+  return launched(ctx, "pd_superpixels");
+}
+
+pd_status pd_pothole_mask(pd_ctx* ctx, const float* D2, const float* D1, const float* D3, int W,
+                          int H, float delta_pd, int mode, uint8_t* mask, double* thresholds,
+                          double* E2) {
+  PD_TRY(begin(ctx));
+  PD_TRY(check_image(ctx, W, H, (size_t)W));
+  PD_REQUIRE(D2 && D1 && D3 && mask, "NULL input or output");
+  PD_REQUIRE(mode == 0 || mode == 1, "mode %d must be 0 or 1", mode);
+  PD_REQUIRE(isfinite(delta_pd), "delta_pd must be finite");
+  PD_TRY(ensure_ws(ctx, threshold_scratch_bytes()));
+  launch_threshold(ctx->stream, D2, D1, D3, W, H, delta_pd, mode, mask, thresholds, E2, ctx->ws);
+  return launched(ctx, "pd_pothole_mask");
+}
+
+pd_status pd_run_pipeline(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H,
+                          size_t pitch, const pd_road_model* model, const pd_params* p,
+                          const pd_outputs* out, pd_stage_times* times) {
+  PD_TRY(begin(ctx));
+  PD_TRY(check_image(ctx, W, H, pitch));
+  PD_TRY(check_model(ctx, model));
+  PD_TRY(check_sgm_params(ctx, p));
+  PD_REQUIRE(W <= kMaxImage && H <= kMaxImage, "the pipeline needs W, H <= %d", kMaxImage);
+  PD_REQUIRE(left && right && out, "NULL input or outputs");
+  PD_REQUIRE(out->d_int && out->D1 && out->D2 && out->labels && out->D3 && out->mask,
+             "pd_outputs is missing a required buffer");
+  PD_REQUIRE(p->model_order == 1 || p->model_order == 2, "model_order must be 1 or 2");
+  PD_REQUIRE(p->slic_K >= 1 && (size_t)p->slic_K <= (size_t)W * H, "slic_K out of range");
+  PD_REQUIRE(isfinite(p->slic_m) && p->slic_m > 0.0f, "slic_m must be positive");
+  PD_REQUIRE(p->slic_iters >= 0 && p->slic_iters <= 1000, "slic_iters out of range");
+  PD_REQUIRE(p->threshold_mode == 0 || p->threshold_mode == 1, "threshold_mode must be 0 or 1");
+  PD_REQUIRE(isfinite(p->delta_dt) && isfinite(p->delta_pd), "non-finite delta");
+  int nx, ny;
+  slic_grid(W, H, p->slic_K, &nx, &ny);
+  size_t need = sgm_scratch_bytes(W, H, p->D, p->paths);
+  size_t other = transform_scratch_bytes(W, H);
+  if (slic_scratch_bytes(nx * ny) > other) other = slic_scratch_bytes(nx * ny);
+  if (threshold_scratch_bytes() > other) other = threshold_scratch_bytes();
+  if (other > need) need = other;
+  PD_TRY(ensure_ws(ctx, need));
+  if (times && !ctx->ev[0])
+    for (auto& e : ctx->ev) PD_TRY(cuda_ok(ctx, cudaEventCreate(&e), "cudaEventCreate"));
+  cudaStream_t s = ctx->stream;
+  pd_prof_rec* rec = prof_begin(ctx);
+  if (times) cudaEventRecord(ctx->ev[0], s);
+  PD_TRY(sgm_enqueue(ctx, left, right, W, H, pitch, model, p, out->kappa, out->d_int, out->D1,
+                     rec));
+  if (times) cudaEventRecord(ctx->ev[1], s);
+  PD_TRY(transform_enqueue(ctx, out->D1, W, H, p->model_order, p->delta_dt, out->fitted,
+                           out->D2, ctx->ws));
+  mark(ctx, rec, 4);
+  if (times) cudaEventRecord(ctx->ev[2], s);
+  launch_slic(s, out->D2, W, H, p->slic_K, p->slic_m, p->slic_iters, out->labels, out->D3,
+              nullptr, ctx->ws);
+  count_launches(ctx, 3 + 2 * (p->slic_iters > 0 ? p->slic_iters : 1));
+  mark(ctx, rec, 5);
+  if (times) cudaEventRecord(ctx->ev[3], s);
+  launch_threshold(s, out->D2, out->D1, out->D3, W, H, p->delta_pd, p->threshold_mode, out->mask,
+                   out->thresholds, nullptr, ctx->ws);
+  count_launches(ctx, 3);
+  mark(ctx, rec, 6);
+  if (times) cudaEventRecord(ctx->ev[4], s);
+  PD_TRY(launched(ctx, "pd_run_pipeline"));
+  if (times) {
+    PD_TRY(cuda_ok(ctx, cudaEventSynchronize(ctx->ev[4]), "pipeline"));
+    cudaEventElapsedTime(&times->sgm_ms, ctx->ev[0], ctx->ev[1]);
+    cudaEventElapsedTime(&times->transform_ms, ctx->ev[1], ctx->ev[2]);
+    cudaEventElapsedTime(&times->superpixel_ms, ctx->ev[2], ctx->ev[3]);
+    cudaEventElapsedTime(&times->mask_ms, ctx->ev[3], ctx->ev[4]);
+    cudaEventElapsedTime(&times->total_ms, ctx->ev[0], ctx->ev[4]);
+  }
+  return PD_OK;
+}
+
+pd_status pd_profile_enable(pd_ctx* ctx, int on) {
+  if (!ctx) return PD_ERR_INVALID_ARG;
+  ctx->prof = on != 0;
+  ctx->nrec = 0;
+  ctx->launches = 0;
+  return PD_OK;
+}
+
+pd_status pd_profile_read(pd_ctx* ctx, pd_profile* out) {
+  PD_TRY(begin(ctx));
+  PD_REQUIRE(out != nullptr, "out is NULL");
+  memset(out, 0, sizeof(*out));
+  double* slot[7] = {nullptr, &out->prep_ms, &out->aggregate_ms, &out->disparity_ms,
+                     &out->transform_ms, &out->superpixel_ms, &out->mask_ms};
+  for (int i = 0; i < ctx->nrec; ++i) {
+    pd_prof_rec& r = ctx->recs[i];
+    int last = -1;
+    for (int k = 0; k < 7; ++k)
+      if (r.used & (1 << k)) last = k;
+    if (last < 1 || !(r.used & 1)) continue;
+    PD_TRY(cuda_ok(ctx, cudaEventSynchronize(r.ev[last]), "pd_profile_read"));
+    int prev = 0;
+    for (int k = 1; k <= last; ++k) {
+      if (!(r.used & (1 << k))) continue;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, r.ev[prev], r.ev[k]);
+      *slot[k] += ms;
+      prev = k;
+    }
+    float tot = 0.f;
+    cudaEventElapsedTime(&tot, r.ev[0], r.ev[last]);
+    out->total_ms += tot;
+    out->calls += 1;
+  }
+  out->launches = ctx->launches;
+  ctx->nrec = 0;
+  ctx->launches = 0;
+  return PD_OK;
+}
+
+}  // extern "C"

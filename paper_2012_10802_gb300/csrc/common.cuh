@@ -1,0 +1,127 @@
+// Internal declarations shared by the libpothole translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "pothole.h"
+
+// Events of one profiled call: start, after prep, after aggregation, end of SGM, after the
+// transform, after SLIC, after the mask.  Unused marks are null.
+struct pd_prof_rec {
+  cudaEvent_t ev[7];
+  int used;  // bitmask of recorded marks
+};
+
+struct pd_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int sm_count = 0;
+  char err[512] = {0};
+  void* ws = nullptr;  // device scratch owned by the context
+  size_t ws_bytes = 0;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  bool prof = false;
+  pd_prof_rec* recs = nullptr;  // kMaxProf records, events created on first use
+  int nrec = 0;
+  long long launches = 0;       // kernels launched by profiled calls
+};
+
+namespace pd {
+
+constexpr int kCensusBits = 24;
+constexpr int kMaxD = 256;
+constexpr int kMaxImage = 4096;  // W, H limit of the exact moment sums
+
+pd_status fail(pd_ctx* c, pd_status st, const char* fmt, ...);
+pd_status cuda_ok(pd_ctx* c, cudaError_t e, const char* what);
+// Checks the last launch; returns PD_OK or PD_ERR_CUDA with the message recorded.
+pd_status launched(pd_ctx* c, const char* what);
+// Makes sure the context holds at least `bytes` of device scratch.
+pd_status ensure_ws(pd_ctx* c, size_t bytes);
+
+// Bump allocator over the context scratch (256-byte aligned pieces).
+struct Carve {
+  char* base;
+  size_t off = 0;
+  explicit Carve(void* b) : base(static_cast<char*>(b)) {}
+  template <class T>
+  T* take(size_t n) {
+    off = (off + 255) & ~size_t(255);
+    T* p = reinterpret_cast<T*>(base + off);
+    off += n * sizeof(T);
+    return p;
+  }
+};
+template <class T>
+inline size_t carve_size(size_t& acc, size_t n) {
+  acc = (acc + 255) & ~size_t(255);
+  acc += n * sizeof(T);
+  return acc;
+}
+
+// Aggregation directions (dx, dy): the first 4 are the axis paths, the last 4 the diagonals.
+struct DirSet {
+  int n;
+  int8_t dx[8];
+  int8_t dy[8];
+};
+DirSet dir_set(int paths);
+DirSet one_dir(int dx, int dy);
+
+// ------------------------------------------------------------------ SGM launchers (sgm.cu)
+void launch_kappa(cudaStream_t s, int W, int H, int order, const double a[3], double cs,
+                  double sn, double delta_pt, int32_t* kappa);
+void launch_warp(cudaStream_t s, const uint8_t* right, int W, int H, size_t pitch,
+                 const int32_t* kappa, uint8_t* out);
+// Census of img, or of the row-shifted image when kappa != nullptr.
+void launch_census(cudaStream_t s, const uint8_t* img, int W, int H, size_t pitch,
+                   const int32_t* kappa, uint32_t* codes);
+// layout 0: natural [H][W][D]; layout 1: the interleaved layout of the aggregation kernels
+// (D % 32 == 0): within each 32-disparity group g, byte 2j holds d = 32g + j and byte 2j+1 holds
+// d = 32g + 16 + j.
+void launch_cost(cudaStream_t s, const uint32_t* cl, const uint32_t* cr, int W, int H, int D,
+                 int layout, uint8_t* cost);
+void launch_to_interleaved(cudaStream_t s, const uint8_t* natural, size_t n_pix, int D,
+                           uint8_t* out);
+void launch_to_natural(cudaStream_t s, const uint8_t* inter, size_t n_pix, int D, uint8_t* out);
+// Eq. (8) for every direction of `dirs`; volume r of `out` (stride vol_bytes) receives L_r in the
+// interleaved layout.
+void launch_aggregate(cudaStream_t s, const uint8_t* cost_il, int W, int H, int D,
+                      const DirSet& dirs, int P1, int P2, uint8_t* out, size_t vol_bytes);
+// S = sum of `ndirs` interleaved L volumes, written as natural uint16 [H][W][D].
+void launch_sum_volumes(cudaStream_t s, const uint8_t* vols, int ndirs, size_t vol_bytes, int W,
+                        int H, int D, uint16_t* S);
+// Winner-take-all + sub-pixel + right-view keys, from interleaved L volumes (S == nullptr) or
+// from a natural uint16 S.  rkeys must hold 0xFFFFFFFF on entry.
+void launch_wta(cudaStream_t s, const uint8_t* vols, int ndirs, size_t vol_bytes,
+                const uint16_t* S, int W, int H, int D, int16_t* d_int, float* dsub,
+                uint32_t* rkeys);
+void launch_lr(cudaStream_t s, const int16_t* d_int, const float* dsub, const uint32_t* rkeys,
+               const int32_t* kappa, int W, int H, int D, int lr_tol, float* D1);
+
+// ------------------------------------------------------------ transform launchers (dt.cu)
+// Float coefficients of f for the D2 kernel, written by the roll solver on the device.
+struct RoadCoefF {
+  float c, s, a0, a1, a2, uc, vc, pad;
+};
+size_t moments_scratch_bytes(int W, int H);
+void launch_moments(cudaStream_t s, const float* D1, int W, int H, void* scratch, int64_t* sums);
+void launch_roll_solve(cudaStream_t s, const int64_t* sums, int order, int W, int H,
+                       pd_road_model* fitted, RoadCoefF* coef);
+void launch_d2(cudaStream_t s, const float* D1, int W, int H, const RoadCoefF* coef,
+               float delta_dt, float* D2);
+
+// ------------------------------------------------------ superpixel / mask (detect.cu)
+void slic_grid(int W, int H, int K, int* nx, int* ny);
+size_t slic_scratch_bytes(int n_centres);
+// Runs seeds + `iters` rounds of assignment/update; writes labels and D3.
+void launch_slic(cudaStream_t s, const float* D2, int W, int H, int K, float m, int iters,
+                 int32_t* labels, float* D3, float* centres_out, void* scratch);
+size_t threshold_scratch_bytes();
+void launch_threshold(cudaStream_t s, const float* D2, const float* D1, const float* D3, int W,
+                      int H, float delta_pd, int mode, uint8_t* mask, double* thresholds,
+                      double* E2, void* scratch);
+
+}  // namespace pd

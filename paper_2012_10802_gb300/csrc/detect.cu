@@ -1,0 +1,391 @@
+// Sec. II-D and II-E on the GPU: SLIC superpixels on the transformed disparity map, the
+// superpixel-clustered map D3, the adaptive threshold of Eqs. (14)-(17) and the pothole mask.
+//
+// SLIC assignment is pixel-parallel: each 16x16 tile first gathers, in index order, the centres
+// whose 2S x 2S search window can reach it, then every pixel scans that short list with the exact
+// window test, so the result equals the centre-by-centre sweep of the original algorithm (the
+// lower index wins ties).  Centre updates use exact integer sums (privatised per tile in shared
+// memory) and one double division per coordinate.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace pd {
+
+namespace {
+
+constexpr int kTile = 16;
+constexpr int kTileThreads = kTile * kTile;
+constexpr int kCandCap = 256;
+
+__device__ __forceinline__ int clampi(int x, int lo, int hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+__device__ float slic_gradient(const float* __restrict__ D2, int W, int H, int x, int y) {
+  float gx = D2[(size_t)y * W + clampi(x + 1, 0, W - 1)] - D2[(size_t)y * W + clampi(x - 1, 0, W - 1)];
+  float gy = D2[(size_t)clampi(y + 1, 0, H - 1) * W + x] - D2[(size_t)clampi(y - 1, 0, H - 1) * W + x];
+  return gx * gx + gy * gy;
+}
+
+// Grid seeds moved to the lowest-gradient pixel of their 3x3 neighbourhood (seed wins ties).
+__global__ void k_slic_seeds(const float* __restrict__ D2, int W, int H, int nx, int ny,
+                             float* __restrict__ cx, float* __restrict__ cy,
+                             float* __restrict__ cv) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nx * ny) return;
+  int i = k % nx, j = k / nx;
+  int sx = (int)(((long long)(2 * i + 1) * W) / (2 * nx));
+  int sy = (int)(((long long)(2 * j + 1) * H) / (2 * ny));
+  int bx = sx, by = sy;
+  float bg = slic_gradient(D2, W, H, sx, sy);
+  for (int dy = -1; dy <= 1; ++dy)
+    for (int dx = -1; dx <= 1; ++dx) {
+      int x = sx + dx, y = sy + dy;
+      if (x < 0 || x >= W || y < 0 || y >= H) continue;
+      float g = slic_gradient(D2, W, H, x, y);
+      if (g < bg) {
+        bg = g;
+        bx = x;
+        by = y;
+      }
+    }
+  cx[k] = (float)bx;
+  cy[k] = (float)by;
+  cv[k] = D2[(size_t)by * W + bx];
+}
+
+__global__ void k_slic_init_labels(int W, int H, int nx, int ny, int32_t* __restrict__ labels) {
+  int x = blockIdx.x * blockDim.x + threadIdx.x;
+  int y = blockIdx.y;
+  if (x >= W) return;
+  labels[(size_t)y * W + x] = (int32_t)(((long long)y * ny / H) * nx + ((long long)x * nx / W));
+}
+
+// One assignment round (if do_assign) plus the per-centre sums of the resulting labels:
+// acc[4k + 0..3] = members, sum x, sum y, sum rint(1024 D2).
+__global__ void __launch_bounds__(kTileThreads) k_slic_assign(
+    const float* __restrict__ D2, int W, int H, int n, const float* __restrict__ cx,
+    const float* __restrict__ cy, const float* __restrict__ cv, float Sf, float coef,
+    int do_assign, int32_t* __restrict__ labels, unsigned long long* __restrict__ acc) {
+  __shared__ int cand[kCandCap];
+  __shared__ float ccx[kCandCap], ccy[kCandCap], ccv[kCandCap];
+  __shared__ unsigned long long sacc[kCandCap][4];
+  __shared__ int wcount[kTileThreads / 32];
+  __shared__ int ncand;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
+  if (tid == 0) ncand = 0;
+  __syncthreads();
+  if (do_assign) {
+    // conservative box test (1 px margin); the exact test runs per pixel below
+    const float bx0 = (float)x0 - 1.0f, bx1 = (float)(x0 + kTile), by0 = (float)y0 - 1.0f,
+                by1 = (float)(y0 + kTile);
+    for (int base = 0; base < n; base += kTileThreads) {
+      int k = base + tid;
+      bool q = false;
+      float fx = 0.f, fy = 0.f;
+      if (k < n) {
+        fx = cx[k];
+        fy = cy[k];
+        q = (fx + Sf >= bx0) && (fx - Sf <= bx1) && (fy + Sf >= by0) && (fy - Sf <= by1);
+      }
+      unsigned bal = __ballot_sync(0xffffffffu, q);
+      if (lane == 0) wcount[warp] = __popc(bal);
+      __syncthreads();
+      int off = ncand;
+      for (int w = 0; w < warp; ++w) off += wcount[w];
+      int pos = off + __popc(bal & ((1u << lane) - 1u));
+      if (q && pos < kCandCap) {
+        cand[pos] = k;
+        ccx[pos] = fx;
+        ccy[pos] = fy;
+        ccv[pos] = cv[k];
+      }
+      __syncthreads();
+      if (tid == 0) {
+        int tot = ncand;
+        for (int w = 0; w < kTileThreads / 32; ++w) tot += wcount[w];
+        ncand = tot;
+      }
+      __syncthreads();
+    }
+  }
+  const int nc = ncand;
+  const bool overflow = nc > kCandCap;
+  for (int i = tid; i < kCandCap; i += kTileThreads)
+    sacc[i][0] = sacc[i][1] = sacc[i][2] = sacc[i][3] = 0ULL;
+  __syncthreads();
+
+  const int x = x0 + (tid % kTile), y = y0 + (tid / kTile);
+  if (x < W && y < H) {
+    const size_t p = (size_t)y * W + x;
+    const float val = D2[p];
+    int lab = labels[p];
+    int slot = -1;
+    if (do_assign) {
+      float best = INFINITY;
+      const float fxp = (float)x, fyp = (float)y;
+      if (!overflow) {
+        for (int i = 0; i < nc; ++i) {
+          float fx = fxp - ccx[i];
+          float fy = fyp - ccy[i];
+          if (!(fabsf(fx) <= Sf && fabsf(fy) <= Sf)) continue;
+          float dv = val - ccv[i];
+          float dd = dv * dv + (fx * fx + fy * fy) * coef;
+          if (dd < best) {
+            best = dd;
+            lab = cand[i];
+            slot = i;
+          }
+        }
+      } else {  // rare: too many candidates for shared memory; scan every centre
+        for (int k = 0; k < n; ++k) {
+          float fx = fxp - cx[k];
+          float fy = fyp - cy[k];
+          if (!(fabsf(fx) <= Sf && fabsf(fy) <= Sf)) continue;
+          float dv = val - cv[k];
+          float dd = dv * dv + (fx * fx + fy * fy) * coef;
+          if (dd < best) {
+            best = dd;
+            lab = k;
+          }
+        }
+      }
+      labels[p] = lab;
+    }
+    long long q = __double2ll_rn((double)val * 1024.0);
+    if (slot >= 0) {
+      atomicAdd(&sacc[slot][0], 1ULL);
+      atomicAdd(&sacc[slot][1], (unsigned long long)x);
+      atomicAdd(&sacc[slot][2], (unsigned long long)y);
+      atomicAdd(&sacc[slot][3], (unsigned long long)q);
+    } else {
+      unsigned long long* a = acc + 4 * (size_t)lab;
+      atomicAdd(a + 0, 1ULL);
+      atomicAdd(a + 1, (unsigned long long)x);
+      atomicAdd(a + 2, (unsigned long long)y);
+      atomicAdd(a + 3, (unsigned long long)q);
+    }
+  }
+  __syncthreads();
+  if (!overflow)
+    for (int i = tid; i < nc; i += kTileThreads) {
+      if (sacc[i][0] == 0ULL) continue;
+      unsigned long long* a = acc + 4 * (size_t)cand[i];
+      atomicAdd(a + 0, sacc[i][0]);
+      atomicAdd(a + 1, sacc[i][1]);
+      atomicAdd(a + 2, sacc[i][2]);
+      atomicAdd(a + 3, sacc[i][3]);
+    }
+}
+
+// Centre update from the exact sums (empty clusters keep their centre); clears the sums.
+__global__ void k_slic_update(int n, unsigned long long* __restrict__ acc, float* __restrict__ cx,
+                              float* __restrict__ cy, float* __restrict__ cv) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  unsigned long long* a = acc + 4 * (size_t)k;
+  long long cnt = (long long)a[0];
+  if (cnt > 0) {
+    cx[k] = (float)((double)(long long)a[1] / (double)cnt);
+    cy[k] = (float)((double)(long long)a[2] / (double)cnt);
+    cv[k] = (float)(((double)(long long)a[3] / (double)cnt) / 1024.0);
+  }
+  a[0] = a[1] = a[2] = a[3] = 0ULL;
+}
+
+// D3: each pixel takes the mean of its superpixel, i.e. the value of the last centre update.
+__global__ void k_slic_d3(const int32_t* __restrict__ labels, const float* __restrict__ cv,
+                          size_t N, float* __restrict__ D3) {
+  size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < N) D3[p] = cv[labels[p]];
+}
+
+__global__ void k_centres_out(int n, const float* __restrict__ cx, const float* __restrict__ cy,
+                              const float* __restrict__ cv, float* __restrict__ out) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  out[3 * k] = cx[k];
+  out[3 * k + 1] = cy[k];
+  out[3 * k + 2] = cv[k];
+}
+
+// ------------------------------------------------------------------- Eqs. (14)-(17)
+constexpr int kBins = 257;  // k = 0..255 plus an overflow bin for everything at or above 32 px
+
+// Histograms of kmax = max(floor(a / 128), floor(b / 1024)) and kmin (the same with min), each
+// with exact sums n, sum a, sum b, sum a^2 + b^2, over interior pixels with a valid 3x3 window;
+// a = rint(1024 D2(p)), b = sum of rint(1024 D2) over the 8 neighbours.  Region 1 of threshold
+// k/8 is {kmax < k}, region 2 is {kmin >= k}.
+__global__ void k_thresh_hist(const float* __restrict__ D2, const float* __restrict__ D1, int W,
+                              int H, unsigned long long* __restrict__ hist /* [2][kBins][4] */) {
+  __shared__ unsigned long long sh[2][kBins][4];
+  for (int i = threadIdx.x; i < 2 * kBins * 4; i += blockDim.x) (&sh[0][0][0])[i] = 0ULL;
+  __syncthreads();
+  int u = blockIdx.x * blockDim.x + threadIdx.x;
+  int v = blockIdx.y;
+  if (u >= 1 && u < W - 1 && v >= 1 && v < H - 1) {
+    bool ok = true;
+    long long a = 0, b = 0;
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        size_t q = (size_t)(v + dy) * W + (u + dx);
+        if (!(D1[q] >= 0.0f)) ok = false;
+        long long qq = __double2ll_rn((double)D2[q] * 1024.0);
+        if (dx == 0 && dy == 0)
+          a = qq;
+        else
+          b += qq;
+      }
+    if (ok) {
+      long long ka = a >> 7, kb = b >> 10;
+      long long kmax = ka > kb ? ka : kb, kmin = ka < kb ? ka : kb;
+      int imax = (int)(kmax < 0 ? 0 : (kmax > 256 ? 256 : kmax));
+      int imin = (int)(kmin < 0 ? 0 : (kmin > 256 ? 256 : kmin));
+      unsigned long long sq = (unsigned long long)(a * a) + (unsigned long long)(b * b);
+      atomicAdd(&sh[0][imax][0], 1ULL);
+      atomicAdd(&sh[0][imax][1], (unsigned long long)a);
+      atomicAdd(&sh[0][imax][2], (unsigned long long)b);
+      atomicAdd(&sh[0][imax][3], sq);
+      atomicAdd(&sh[1][imin][0], 1ULL);
+      atomicAdd(&sh[1][imin][1], (unsigned long long)a);
+      atomicAdd(&sh[1][imin][2], (unsigned long long)b);
+      atomicAdd(&sh[1][imin][3], sq);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * kBins * 4; i += blockDim.x) {
+    unsigned long long x = (&sh[0][0][0])[i];
+    if (x) atomicAdd(hist + i, x);
+  }
+}
+
+// E2(t) of Eq. (17) for t = k/8, k = 1..255, from prefix (region 1) and suffix (region 2) sums;
+// t_r = smallest minimiser; t_s from mode.  One thread, 255 steps.
+__global__ void k_thresh_solve(const unsigned long long* __restrict__ hist, float delta_pd,
+                               int mode, double* __restrict__ thr, double* __restrict__ E2) {
+  if (threadIdx.x != 0) return;
+  const unsigned long long(*hmax)[4] = reinterpret_cast<const unsigned long long(*)[4]>(hist);
+  const unsigned long long(*hmin)[4] = reinterpret_cast<const unsigned long long(*)[4]>(hist + kBins * 4);
+  long long n2 = 0, a2 = 0, b2 = 0;
+  unsigned long long s2 = 0;
+  for (int j = 1; j < kBins; ++j) {  // region 2 at k = 1: kmin >= 1
+    n2 += (long long)hmin[j][0];
+    a2 += (long long)hmin[j][1];
+    b2 += (long long)hmin[j][2];
+    s2 += hmin[j][3];
+  }
+  long long n1 = (long long)hmax[0][0], a1 = (long long)hmax[0][1], b1 = (long long)hmax[0][2];
+  unsigned long long s1 = hmax[0][3];
+  int best = -1;
+  double bestE = 0.0, bestMean = 0.0;
+  if (E2) E2[0] = NAN;
+  for (int k = 1; k < 256; ++k) {
+    double e = NAN;
+    if (n1 != 0 && n2 != 0) {
+      double e1 = (double)s1 - ((double)a1 * (double)a1 + (double)b1 * (double)b1) / (double)n1;
+      double e2 = (double)s2 - ((double)a2 * (double)a2 + (double)b2 * (double)b2) / (double)n2;
+      e = e1 + e2;
+      if (best < 0 || e < bestE) {
+        best = k;
+        bestE = e;
+        bestMean = ((double)a2 / (double)n2) / 1024.0;
+      }
+    }
+    if (E2) E2[k] = e;
+    // move to k + 1: region 1 gains bin k of kmax, region 2 loses bin k of kmin
+    n1 += (long long)hmax[k][0];
+    a1 += (long long)hmax[k][1];
+    b1 += (long long)hmax[k][2];
+    s1 += hmax[k][3];
+    n2 -= (long long)hmin[k][0];
+    a2 -= (long long)hmin[k][1];
+    b2 -= (long long)hmin[k][2];
+    s2 -= hmin[k][3];
+  }
+  if (best < 0) {
+    thr[0] = NAN;
+    thr[1] = -INFINITY;
+    return;
+  }
+  thr[0] = (double)best * 0.125;
+  thr[1] = (mode == 0 ? bestMean : thr[0]) - (double)delta_pd;
+}
+
+__global__ void k_mask(const float* __restrict__ D3, size_t N, const double* __restrict__ thr,
+                       uint8_t* __restrict__ mask) {
+  size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  double ts = thr[1];
+  mask[p] = (double)D3[p] < ts ? 1 : 0;
+}
+
+}  // namespace
+
+void slic_grid(int W, int H, int K, int* nx, int* ny) {
+  double S = sqrt((double)W * (double)H / (double)K);
+  int a = (int)floor((double)W / S + 0.5);
+  int b = (int)floor((double)H / S + 0.5);
+  a = a < 1 ? 1 : (a > W ? W : a);
+  b = b < 1 ? 1 : (b > H ? H : b);
+  *nx = a;
+  *ny = b;
+}
+
+size_t slic_scratch_bytes(int n) {
+  size_t acc = 0;
+  carve_size<float>(acc, n);
+  carve_size<float>(acc, n);
+  carve_size<float>(acc, n);
+  carve_size<unsigned long long>(acc, 4 * (size_t)n);
+  return acc;
+}
+
+void launch_slic(cudaStream_t s, const float* D2, int W, int H, int K, float m, int iters,
+                 int32_t* labels, float* D3, float* centres_out, void* scratch) {
+  int nx, ny;
+  slic_grid(W, H, K, &nx, &ny);
+  int n = nx * ny;
+  Carve cv_(scratch);
+  float* cx = cv_.take<float>(n);
+  float* cy = cv_.take<float>(n);
+  float* cv = cv_.take<float>(n);
+  unsigned long long* acc = cv_.take<unsigned long long>(4 * (size_t)n);
+  float Sf = (float)sqrt((double)W * (double)H / (double)K);
+  float coef = (float)((double)m * (double)m * (double)K / ((double)W * (double)H));
+  cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 4 * (size_t)n, s);
+  k_slic_seeds<<<(n + 127) / 128, 128, 0, s>>>(D2, W, H, nx, ny, cx, cy, cv);
+  k_slic_init_labels<<<dim3((W + 255) / 256, H), 256, 0, s>>>(W, H, nx, ny, labels);
+  dim3 tiles((W + kTile - 1) / kTile, (H + kTile - 1) / kTile);
+  int rounds = iters > 0 ? iters : 1;
+  for (int it = 0; it < rounds; ++it) {
+    k_slic_assign<<<tiles, kTileThreads, 0, s>>>(D2, W, H, n, cx, cy, cv, Sf, coef,
+                                                 iters > 0 ? 1 : 0, labels, acc);
+    k_slic_update<<<(n + 127) / 128, 128, 0, s>>>(n, acc, cx, cy, cv);
+  }
+  size_t N = (size_t)W * H;
+  k_slic_d3<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(labels, cv, N, D3);
+  if (centres_out) k_centres_out<<<(n + 127) / 128, 128, 0, s>>>(n, cx, cy, cv, centres_out);
+}
+
+size_t threshold_scratch_bytes() {
+  size_t acc = 0;
+  carve_size<unsigned long long>(acc, 2 * kBins * 4);
+  carve_size<double>(acc, 2);
+  return acc;
+}
+
+void launch_threshold(cudaStream_t s, const float* D2, const float* D1, const float* D3, int W,
+                      int H, float delta_pd, int mode, uint8_t* mask, double* thresholds,
+                      double* E2, void* scratch) {
+  Carve c(scratch);
+  unsigned long long* hist = c.take<unsigned long long>(2 * kBins * 4);
+  double* thr = c.take<double>(2);
+  if (thresholds) thr = thresholds;
+  cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * 2 * kBins * 4, s);
+  k_thresh_hist<<<dim3((W + 255) / 256, H), 256, 0, s>>>(D2, D1, W, H, hist);
+  k_thresh_solve<<<1, 32, 0, s>>>(hist, delta_pd, mode, thr, E2);
+  size_t N = (size_t)W * H;
+  k_mask<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(D3, N, thr, mask);
+}
+
+}  // namespace pd

@@ -1,0 +1,576 @@
+// Sec. II-A and II-B on the GPU: row shifts (Eq. (6)), the perspective warp, census cost,
+// Eq. (8) aggregation, Eq. (9) winner-take-all with sub-pixel step and left-right check, Eq. (10).
+//
+// Aggregation design: every path of every direction is an independent dynamic-programming line.
+// A line is owned by G = D/32 lanes of a warp; each lane keeps 32 disparities as 16 packed
+// u16x2 words, word j holding (d = 32g + j, d = 32g + 16 + j).  With that pairing the d-1 / d+1
+// neighbours of word j are words j-1 / j+1, so the recurrence needs no byte shuffling: per word it
+// is one 3-input min, one fused add-min and one add (Hopper/Blackwell DPX instructions), and only
+// the two ends of a lane's range cross lanes.  The matching cost is computed once per (p, d) into
+// a uint8 volume (popcount is a quarter-rate instruction) and every direction reads it with 16-byte
+// loads.
+#include <cstdio>
+
+#include "common.cuh"
+
+namespace pd {
+
+namespace {
+
+constexpr uint32_t kFull = 0xffffffffu;
+constexpr uint32_t kBig2 = 0x3fff3fffu;  // "no neighbour": never the minimum, no u16 overflow
+
+__device__ __forceinline__ int clampi(int x, int lo, int hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+// ----------------------------------------------------------------------------- Eq. (6)
+// One warp per row: brute-force minimum of f(x, v) - delta_pt over x, evaluated in double in the
+// fixed operation order of the model definition (the library is built without FMA contraction).
+__global__ void k_kappa(int W, int H, int order, double a0, double a1, double a2, double cs,
+                        double sn, double delta_pt, int32_t* __restrict__ kappa) {
+  int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  if (v >= H) return;
+  double uc = (double)(W - 1) * 0.5, vc = (double)(H - 1) * 0.5;
+  double t1 = ((double)v - vc) * cs;
+  double best = 1e300;
+  for (int x = lane; x < W; x += 32) {
+    double t2 = ((double)x - uc) * sn;
+    double vp = (t1 - t2) + vc;
+    double f = a0 + a1 * vp;
+    if (order == 2) f = f + a2 * (vp * vp);
+    f = f - delta_pt;
+    best = f < best ? f : best;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    double other = __shfl_xor_sync(kFull, best, o);
+    best = other < best ? other : best;
+  }
+  if (lane == 0) kappa[v] = (int32_t)floor(best);
+}
+
+__global__ void k_warp(const uint8_t* __restrict__ right, int W, int H, size_t pitch,
+                       const int32_t* __restrict__ kappa, uint8_t* __restrict__ out) {
+  int u = blockIdx.x * blockDim.x + threadIdx.x;
+  int v = blockIdx.y;
+  if (u >= W) return;
+  out[(size_t)v * pitch + u] = right[(size_t)v * pitch + clampi(u - kappa[v], 0, W - 1)];
+}
+
+// ----------------------------------------------------------------------------- census
+constexpr int kCT_W = 32, kCT_H = 8;
+
+__global__ void k_census(const uint8_t* __restrict__ img, int W, int H, size_t pitch,
+                         const int32_t* __restrict__ kappa, uint32_t* __restrict__ codes) {
+  __shared__ uint8_t tile[kCT_H + 4][kCT_W + 4];
+  int u0 = blockIdx.x * kCT_W, v0 = blockIdx.y * kCT_H;
+  for (int i = threadIdx.y * kCT_W + threadIdx.x; i < (kCT_H + 4) * (kCT_W + 4);
+       i += kCT_W * kCT_H) {
+    int ty = i / (kCT_W + 4), tx = i % (kCT_W + 4);
+    int y = clampi(v0 + ty - 2, 0, H - 1);
+    int x = clampi(u0 + tx - 2, 0, W - 1);
+    if (kappa) x = clampi(x - kappa[y], 0, W - 1);  // the row-shifted image at (x, y)
+    tile[ty][tx] = img[(size_t)y * pitch + x];
+  }
+  __syncthreads();
+  int u = u0 + threadIdx.x, v = v0 + threadIdx.y;
+  if (u >= W || v >= H) return;
+  uint8_t c = tile[threadIdx.y + 2][threadIdx.x + 2];
+  uint32_t code = 0;
+  int k = 0;
+#pragma unroll
+  for (int dy = 0; dy < 5; ++dy)
+#pragma unroll
+    for (int dx = 0; dx < 5; ++dx) {
+      if (dx == 2 && dy == 2) continue;
+      code |= (uint32_t)(tile[threadIdx.y + dy][threadIdx.x + dx] < c) << k;
+      ++k;
+    }
+  codes[(size_t)v * W + u] = code;
+}
+
+// ----------------------------------------------------------------------------- cost
+// Interleaved layout, D % 32 == 0: one thread per (pixel, 32-disparity group), 32 bytes out.
+constexpr int kCostThreads = 256;
+
+__global__ void __launch_bounds__(kCostThreads) k_cost_il(const uint32_t* __restrict__ cl,
+                                                          const uint32_t* __restrict__ cr, int W,
+                                                          int D, uint8_t* __restrict__ cost) {
+  __shared__ uint32_t sR[kCostThreads + kMaxD];
+  const int groups = D >> 5;
+  const int P = kCostThreads / groups;  // pixels per block
+  const int v = blockIdx.y;
+  const int u0 = blockIdx.x * P;
+  const int base = u0 - D + 1;
+  for (int i = threadIdx.x; i < P + D - 1; i += kCostThreads) {
+    int x = base + i;
+    sR[i] = (x >= 0 && x < W) ? cr[(size_t)v * W + x] : 0u;
+  }
+  __syncthreads();
+  const int u = u0 + threadIdx.x / groups;
+  const int g = threadIdx.x % groups;
+  if (u >= W) return;
+  const uint32_t c0 = cl[(size_t)v * W + u];
+  uint32_t w[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    uint32_t packed = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int p = 4 * i + b;
+      int d = 32 * g + (p >> 1) + ((p & 1) << 4);
+      int x = u - d;
+      uint32_t c = x >= 0 ? (uint32_t)__popc(c0 ^ sR[x - base]) : (uint32_t)kCensusBits;
+      packed |= c << (8 * b);
+    }
+    w[i] = packed;
+  }
+  uint4* dst = reinterpret_cast<uint4*>(cost + ((size_t)v * W + u) * D + 32 * g);
+  dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+  dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+// Natural layout, any 1 <= D <= 256: one thread per (pixel, d).
+__global__ void __launch_bounds__(kCostThreads) k_cost_nat(const uint32_t* __restrict__ cl,
+                                                           const uint32_t* __restrict__ cr, int W,
+                                                           int D, uint8_t* __restrict__ cost) {
+  __shared__ uint32_t sR[kCostThreads + kMaxD];
+  __shared__ uint32_t sL[kCostThreads];
+  const int v = blockIdx.y;
+  const size_t row0 = (size_t)v * W * D;
+  const size_t first = (size_t)blockIdx.x * kCostThreads;  // first (u, d) index in the row
+  const int u0 = (int)(first / D);
+  const int ulast = (int)min((first + kCostThreads - 1) / D, (size_t)W - 1);
+  const int base = u0 - D + 1;
+  for (int i = threadIdx.x; i < ulast - base + 1; i += kCostThreads) {
+    int x = base + i;
+    sR[i] = (x >= 0 && x < W) ? cr[(size_t)v * W + x] : 0u;
+  }
+  for (int i = threadIdx.x; i < ulast - u0 + 1; i += kCostThreads) sL[i] = cl[(size_t)v * W + u0 + i];
+  __syncthreads();
+  size_t idx = first + threadIdx.x;
+  if (idx >= (size_t)W * D) return;
+  int u = (int)(idx / D), d = (int)(idx % D);
+  int x = u - d;
+  uint8_t c = x >= 0 ? (uint8_t)__popc(sL[u - u0] ^ sR[x - base]) : (uint8_t)kCensusBits;
+  cost[row0 + idx] = c;
+}
+
+// Natural <-> interleaved byte order within each 32-disparity group.
+__global__ void k_to_interleaved(const uint8_t* __restrict__ in, size_t n_groups,
+                                 uint8_t* __restrict__ out) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_groups) return;
+  const uint4* s = reinterpret_cast<const uint4*>(in + 32 * t);
+  uint4 a = s[0], b = s[1];
+  uint32_t n[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+  uint32_t o[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    o[i] = __byte_perm(n[i >> 1], n[4 + (i >> 1)], (i & 1) ? 0x7362 : 0x5140);
+  uint4* d = reinterpret_cast<uint4*>(out + 32 * t);
+  d[0] = make_uint4(o[0], o[1], o[2], o[3]);
+  d[1] = make_uint4(o[4], o[5], o[6], o[7]);
+}
+
+__global__ void k_to_natural(const uint8_t* __restrict__ in, size_t n_groups,
+                             uint8_t* __restrict__ out) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_groups) return;
+  const uint4* s = reinterpret_cast<const uint4*>(in + 32 * t);
+  uint4 a = s[0], b = s[1];
+  uint32_t r[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+  uint32_t o[8];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    o[i] = __byte_perm(r[2 * i], r[2 * i + 1], 0x6420);
+    o[4 + i] = __byte_perm(r[2 * i], r[2 * i + 1], 0x7531);
+  }
+  uint4* d = reinterpret_cast<uint4*>(out + 32 * t);
+  d[0] = make_uint4(o[0], o[1], o[2], o[3]);
+  d[1] = make_uint4(o[4], o[5], o[6], o[7]);
+}
+
+// ----------------------------------------------------------------------------- Eq. (8)
+constexpr int kAggWarps = 4;
+
+struct LineGeom {
+  int dx, dy, nlines, nsteps, vlo, vhi;
+};
+
+__device__ __forceinline__ void line_pixel(const LineGeom& L, int W, int H, int line, int s,
+                                           int& u, int& v, bool& act) {
+  if (L.dy == 0) {
+    v = line;
+    u = L.dx > 0 ? s : W - 1 - s;
+    act = line < L.nlines;
+  } else {
+    v = L.dy > 0 ? L.vlo + s : L.vhi - s;
+    u = L.dx == 0 ? line : (L.dx == L.dy ? line - (H - 1) + v : line - v);
+    act = line < L.nlines && u >= 0 && u < W;
+  }
+}
+
+template <int G>
+__global__ void __launch_bounds__(kAggWarps * 32) k_aggregate(const uint8_t* __restrict__ cost,
+                                                              uint8_t* __restrict__ out, int W,
+                                                              int H, int D, DirSet dirs,
+                                                              uint32_t P1x2, uint32_t K21x2,
+                                                              size_t vol_bytes) {
+  constexpr int LPW = 32 / G;  // lines per warp
+  const int r = blockIdx.y;
+  LineGeom L;
+  L.dx = dirs.dx[r];
+  L.dy = dirs.dy[r];
+  if (L.dy == 0) {
+    L.nlines = H;
+    L.nsteps = W;
+  } else if (L.dx == 0) {
+    L.nlines = W;
+    L.nsteps = H;
+  } else {
+    L.nlines = W + H - 1;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane % G;
+  const int first = (blockIdx.x * kAggWarps + warp) * LPW;
+  if (first >= L.nlines) return;  // the whole warp leaves together
+  const int line = first + lane / G;
+  const int last = min(first + LPW, L.nlines) - 1;
+  L.vlo = 0;
+  L.vhi = H - 1;
+  if (L.dy != 0 && L.dx != 0) {
+    if (L.dx == L.dy) {  // u - v constant
+      L.vlo = max(0, H - 1 - last);
+      L.vhi = min(H - 1, W + H - 2 - first);
+    } else {  // u + v constant
+      L.vlo = max(0, first - W + 1);
+      L.vhi = min(H - 1, last);
+    }
+    L.nsteps = L.vhi - L.vlo + 1;
+  }
+  uint8_t* dst_vol = out + (size_t)r * vol_bytes;
+
+  uint32_t N[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) N[j] = 0;
+
+  int u, v;
+  bool act;
+  line_pixel(L, W, H, line, 0, u, v, act);
+  uint4 ca = make_uint4(0, 0, 0, 0), cb = ca;
+  if (act) {
+    const uint4* src = reinterpret_cast<const uint4*>(cost + ((size_t)v * W + u) * D + 32 * g);
+    ca = __ldg(src);
+    cb = __ldg(src + 1);
+  }
+  for (int s = 0; s < L.nsteps; ++s) {
+    int un, vn;
+    bool actn;
+    line_pixel(L, W, H, line, s + 1, un, vn, actn);
+    actn = actn && s + 1 < L.nsteps;
+    uint4 na = make_uint4(0, 0, 0, 0), nb = na;
+    if (actn) {
+      const uint4* src = reinterpret_cast<const uint4*>(cost + ((size_t)vn * W + un) * D + 32 * g);
+      na = __ldg(src);
+      nb = __ldg(src + 1);
+    }
+    const uint32_t raw[8] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+    // neighbours across the lane boundaries of this line's lane group
+    uint32_t prevHi = kBig2, nextLo = kBig2;
+    if constexpr (G > 1) {
+      uint32_t up = __shfl_up_sync(kFull, N[15], 1, G);
+      uint32_t dn = __shfl_down_sync(kFull, N[0], 1, G);
+      if (g > 0) prevHi = up;
+      if (g < G - 1) nextLo = dn;
+    }
+    const uint32_t left0 = __byte_perm(prevHi, N[15], 0x5432);
+    const uint32_t right15 = __byte_perm(N[0], nextLo, 0x5432);
+    uint32_t Lw[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      uint32_t lft = j == 0 ? left0 : N[j - 1];
+      uint32_t rgt = j == 15 ? right15 : N[j + 1];
+      uint32_t t = __vimin3_u16x2(lft, rgt, K21x2);
+      t = __viaddmin_u16x2(t, P1x2, N[j]);
+      uint32_t c = __byte_perm(raw[j >> 1], 0, (j & 1) ? 0x4342 : 0x4140);
+      Lw[j] = __vadd2(t, c);
+    }
+    uint32_t m8[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) m8[j] = __vminu2(Lw[2 * j], Lw[2 * j + 1]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) m8[j] = __vminu2(m8[j], m8[j + 4]);
+    uint32_t m = __vminu2(__vminu2(m8[0], m8[1]), __vminu2(m8[2], m8[3]));
+    m = __vminu2(m, __byte_perm(m, m, 0x1032));  // both halves = min of the two halves
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) m = __vminu2(m, __shfl_xor_sync(kFull, m, o, G));
+    if (act) {
+      uint32_t w[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) w[i] = __byte_perm(Lw[2 * i], Lw[2 * i + 1], 0x6420);
+      uint4* dst = reinterpret_cast<uint4*>(dst_vol + ((size_t)v * W + u) * D + 32 * g);
+      __stcs(dst, make_uint4(w[0], w[1], w[2], w[3]));
+      __stcs(dst + 1, make_uint4(w[4], w[5], w[6], w[7]));
+#pragma unroll
+      for (int j = 0; j < 16; ++j) N[j] = __vsub2(Lw[j], m);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) N[j] = 0;
+    }
+    ca = na;
+    cb = nb;
+    u = un;
+    v = vn;
+    act = actn;
+  }
+}
+
+// ------------------------------------------------------------- volume sums and Eq. (9)
+constexpr int kWtaThreads = 128;
+
+// Loads this thread's 32 disparities of S as planar u16x2 pairs (d = 32g + j, 32g + 16 + j).
+__device__ __forceinline__ void load_S_il(const uint8_t* __restrict__ vols, int ndirs,
+                                          size_t vol_bytes, size_t off, uint32_t sw[16]) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) sw[j] = 0;
+  for (int r = 0; r < ndirs; ++r) {
+    const uint4* src = reinterpret_cast<const uint4*>(vols + (size_t)r * vol_bytes + off);
+    uint4 a = __ldcs(src), b = __ldcs(src + 1);
+    const uint32_t raw[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      sw[j] = __vadd2(sw[j], __byte_perm(raw[j >> 1], 0, (j & 1) ? 0x4342 : 0x4140));
+  }
+}
+
+__device__ __forceinline__ void load_S_nat(const uint16_t* __restrict__ S, size_t off,
+                                           uint32_t sw[16]) {
+  const uint4* src = reinterpret_cast<const uint4*>(S + off);
+  uint32_t n[16];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    uint4 q = __ldg(src + i);
+    n[4 * i] = q.x;
+    n[4 * i + 1] = q.y;
+    n[4 * i + 2] = q.z;
+    n[4 * i + 3] = q.w;
+  }
+  // n[k] holds d = 2k, 2k+1 (relative to the group)
+#pragma unroll
+  for (int j = 0; j < 16; ++j)
+    sw[j] = __byte_perm(n[j >> 1], n[8 + (j >> 1)], (j & 1) ? 0x7632 : 0x5410);
+}
+
+__global__ void __launch_bounds__(kWtaThreads) k_sum_volumes(const uint8_t* __restrict__ vols,
+                                                             int ndirs, size_t vol_bytes,
+                                                             size_t n_groups,
+                                                             uint16_t* __restrict__ S) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_groups) return;
+  uint32_t sw[16];
+  load_S_il(vols, ndirs, vol_bytes, 32 * t, sw);
+  uint32_t o[16];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    o[k] = __byte_perm(sw[2 * k], sw[2 * k + 1], 0x5410);
+    o[8 + k] = __byte_perm(sw[2 * k], sw[2 * k + 1], 0x7632);
+  }
+  uint4* d = reinterpret_cast<uint4*>(S + 32 * t);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) d[i] = make_uint4(o[4 * i], o[4 * i + 1], o[4 * i + 2], o[4 * i + 3]);
+}
+
+// One block covers P = 128 / G pixels of one row; G = D / 32 threads per pixel.
+// Writes d* (int16) and the sub-pixel value, and folds the right-view candidates of its pixels
+// into rkeys[v][x] = min over d of (S(x + d, d) << 8 | d) with one atomicMin per covered x.
+__global__ void __launch_bounds__(kWtaThreads) k_wta(const uint8_t* __restrict__ vols, int ndirs,
+                                                     size_t vol_bytes,
+                                                     const uint16_t* __restrict__ S, int W, int D,
+                                                     int16_t* __restrict__ d_int,
+                                                     float* __restrict__ dsub,
+                                                     uint32_t* __restrict__ rkeys) {
+  extern __shared__ uint16_t sS[];  // [P][D]
+  const int G = D >> 5;
+  const int P = kWtaThreads / G;
+  const int v = blockIdx.y;
+  const int u0 = blockIdx.x * P;
+  const int Peff = min(P, W - u0);
+  const int pix = threadIdx.x / G, g = threadIdx.x % G;
+  const int u = u0 + pix;
+  uint32_t key = 0xffffffffu;
+  if (pix < Peff) {
+    size_t off = ((size_t)v * W + u) * D + 32 * g;
+    uint32_t sw[16];
+    if (S)
+      load_S_nat(S, off, sw);
+    else
+      load_S_il(vols, ndirs, vol_bytes, off, sw);
+    uint16_t* row = sS + pix * D + 32 * g;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      reinterpret_cast<uint32_t*>(row)[k] = __byte_perm(sw[2 * k], sw[2 * k + 1], 0x5410);
+      reinterpret_cast<uint32_t*>(row + 16)[k] = __byte_perm(sw[2 * k], sw[2 * k + 1], 0x7632);
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      uint32_t klo = ((sw[j] & 0xffffu) << 8) | (uint32_t)(32 * g + j);
+      uint32_t khi = ((sw[j] >> 16) << 8) | (uint32_t)(32 * g + 16 + j);
+      key = min(key, min(klo, khi));
+    }
+  }
+  for (int o = 1; o < G; o <<= 1) key = min(key, __shfl_xor_sync(kFull, key, o, G));
+  __syncthreads();
+  if (pix < Peff && g == 0) {
+    int ds = (int)(key & 0xffu);
+    float sub = (float)ds;
+    if (ds > 0 && ds < D - 1) {
+      int a = sS[pix * D + ds - 1], b = sS[pix * D + ds], c = sS[pix * D + ds + 1];
+      int num = a - c;
+      int den = 2 * (a + c - 2 * b);
+      if (den > 0) sub = (float)ds + (float)num / (float)den;
+    }
+    d_int[(size_t)v * W + u] = (int16_t)ds;
+    dsub[(size_t)v * W + u] = sub;
+  }
+  // right view: x in [u0 - D + 1, u0 + Peff - 1], candidates d with u0 <= x + d < u0 + Peff
+  for (int i = threadIdx.x; i < Peff + D - 1; i += kWtaThreads) {
+    int x = u0 - D + 1 + i;
+    if (x < 0) continue;
+    int dlo = max(0, u0 - x);
+    int dhi = min(D - 1, u0 + Peff - 1 - x);
+    uint32_t best = 0xffffffffu;
+    for (int d = dlo; d <= dhi; ++d) {
+      uint32_t k = ((uint32_t)sS[(x + d - u0) * D + d] << 8) | (uint32_t)d;
+      best = k < best ? k : best;
+    }
+    if (dlo <= dhi) atomicMin(rkeys + (size_t)v * W + x, best);
+  }
+}
+
+__global__ void k_lr(const int16_t* __restrict__ d_int, const float* __restrict__ dsub,
+                     const uint32_t* __restrict__ rkeys, const int32_t* __restrict__ kappa, int W,
+                     int H, int D, int lr_tol, float* __restrict__ D1) {
+  int u = blockIdx.x * blockDim.x + threadIdx.x;
+  int v = blockIdx.y;
+  if (u >= W) return;
+  size_t p = (size_t)v * W + u;
+  int ds = d_int[p];
+  int xr = u - ds;
+  bool valid = u >= D - 1 && xr >= 0;
+  if (valid) {
+    int dr = (int)(rkeys[(size_t)v * W + xr] & 0xffu);
+    valid = abs(ds - dr) <= lr_tol;
+  }
+  float d1 = dsub[p] + (float)kappa[v];
+  D1[p] = (valid && d1 >= 0.0f) ? d1 : -1.0f;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ launchers
+
+DirSet dir_set(int paths) {
+  static const int8_t dx[8] = {1, -1, 0, 0, 1, -1, 1, -1};
+  static const int8_t dy[8] = {0, 0, 1, -1, 1, -1, -1, 1};
+  DirSet d;
+  d.n = paths;
+  for (int i = 0; i < 8; ++i) {
+    d.dx[i] = dx[i];
+    d.dy[i] = dy[i];
+  }
+  return d;
+}
+
+DirSet one_dir(int dx, int dy) {
+  DirSet d = dir_set(1);
+  d.dx[0] = (int8_t)dx;
+  d.dy[0] = (int8_t)dy;
+  return d;
+}
+
+void launch_kappa(cudaStream_t s, int W, int H, int order, const double a[3], double cs,
+                  double sn, double delta_pt, int32_t* kappa) {
+  k_kappa<<<(H + 3) / 4, 128, 0, s>>>(W, H, order, a[0], a[1], a[2], cs, sn, delta_pt, kappa);
+}
+
+void launch_warp(cudaStream_t s, const uint8_t* right, int W, int H, size_t pitch,
+                 const int32_t* kappa, uint8_t* out) {
+  dim3 grid((W + 255) / 256, H);
+  k_warp<<<grid, 256, 0, s>>>(right, W, H, pitch, kappa, out);
+}
+
+void launch_census(cudaStream_t s, const uint8_t* img, int W, int H, size_t pitch,
+                   const int32_t* kappa, uint32_t* codes) {
+  dim3 grid((W + kCT_W - 1) / kCT_W, (H + kCT_H - 1) / kCT_H);
+  k_census<<<grid, dim3(kCT_W, kCT_H), 0, s>>>(img, W, H, pitch, kappa, codes);
+}
+
+void launch_cost(cudaStream_t s, const uint32_t* cl, const uint32_t* cr, int W, int H, int D,
+                 int layout, uint8_t* cost) {
+  if (layout == 1) {
+    int P = kCostThreads / (D / 32);
+    dim3 grid((W + P - 1) / P, H);
+    k_cost_il<<<grid, kCostThreads, 0, s>>>(cl, cr, W, D, cost);
+  } else {
+    size_t per_row = (size_t)W * D;
+    dim3 grid((unsigned)((per_row + kCostThreads - 1) / kCostThreads), H);
+    k_cost_nat<<<grid, kCostThreads, 0, s>>>(cl, cr, W, D, cost);
+  }
+}
+
+void launch_to_interleaved(cudaStream_t s, const uint8_t* natural, size_t n_pix, int D,
+                           uint8_t* out) {
+  size_t n = n_pix * (size_t)(D / 32);
+  k_to_interleaved<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(natural, n, out);
+}
+
+void launch_to_natural(cudaStream_t s, const uint8_t* inter, size_t n_pix, int D, uint8_t* out) {
+  size_t n = n_pix * (size_t)(D / 32);
+  k_to_natural<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(inter, n, out);
+}
+
+void launch_aggregate(cudaStream_t s, const uint8_t* cost_il, int W, int H, int D,
+                      const DirSet& dirs, int P1, int P2, uint8_t* out, size_t vol_bytes) {
+  int G = D / 32;
+  int maxlines = 0;
+  for (int r = 0; r < dirs.n; ++r) {
+    int n = dirs.dy[r] == 0 ? H : (dirs.dx[r] == 0 ? W : W + H - 1);
+    maxlines = n > maxlines ? n : maxlines;
+  }
+  int lines_per_block = kAggWarps * (32 / G);
+  dim3 grid((maxlines + lines_per_block - 1) / lines_per_block, dirs.n);
+  uint32_t P1x2 = (uint32_t)P1 * 0x10001u;
+  uint32_t K21x2 = (uint32_t)(P2 - P1) * 0x10001u;
+  switch (G) {
+    case 1: k_aggregate<1><<<grid, kAggWarps * 32, 0, s>>>(cost_il, out, W, H, D, dirs, P1x2, K21x2, vol_bytes); break;
+    case 2: k_aggregate<2><<<grid, kAggWarps * 32, 0, s>>>(cost_il, out, W, H, D, dirs, P1x2, K21x2, vol_bytes); break;
+    case 4: k_aggregate<4><<<grid, kAggWarps * 32, 0, s>>>(cost_il, out, W, H, D, dirs, P1x2, K21x2, vol_bytes); break;
+    case 8: k_aggregate<8><<<grid, kAggWarps * 32, 0, s>>>(cost_il, out, W, H, D, dirs, P1x2, K21x2, vol_bytes); break;
+    default: break;  // the API admits D in {32, 64, 128, 256} only
+  }
+}
+
+void launch_sum_volumes(cudaStream_t s, const uint8_t* vols, int ndirs, size_t vol_bytes, int W,
+                        int H, int D, uint16_t* S) {
+  size_t n = (size_t)W * H * (D / 32);
+  k_sum_volumes<<<(unsigned)((n + kWtaThreads - 1) / kWtaThreads), kWtaThreads, 0, s>>>(
+      vols, ndirs, vol_bytes, n, S);
+}
+
+void launch_wta(cudaStream_t s, const uint8_t* vols, int ndirs, size_t vol_bytes,
+                const uint16_t* S, int W, int H, int D, int16_t* d_int, float* dsub,
+                uint32_t* rkeys) {
+  int G = D / 32;
+  int P = kWtaThreads / G;
+  dim3 grid((W + P - 1) / P, H);
+  size_t smem = (size_t)P * D * sizeof(uint16_t);
+  k_wta<<<grid, kWtaThreads, smem, s>>>(vols, ndirs, vol_bytes, S, W, D, d_int, dsub, rkeys);
+}
+
+void launch_lr(cudaStream_t s, const int16_t* d_int, const float* dsub, const uint32_t* rkeys,
+               const int32_t* kappa, int W, int H, int D, int lr_tol, float* D1) {
+  dim3 grid((W + 255) / 256, H);
+  k_lr<<<grid, 256, 0, s>>>(d_int, dsub, rkeys, kappa, W, H, D, lr_tol, D1);
+}
+
+}  // namespace pd
