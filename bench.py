@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--size", default=None,
+                    help="WxH of a smaller road for profiling captures (not a benchmark line)")
     return ap.parse_args()
 
 
@@ -167,6 +169,9 @@ def run_reference(args, rank, world):
 
 def main():
     args = parse()
+    global W_, H_
+    if args.size:
+        W_, H_ = (int(x) for x in args.size.lower().split("x"))
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -190,7 +195,8 @@ def main():
         torch.cuda.synchronize()
 
     # inputs: one synthetic pair per rank (independent frames: weak scaling, no collective)
-    sc = synth.road_1280x720(seed=2 + rank)
+    sc = synth.road_1280x720(seed=2 + rank) if (W_, H_) == (1280, 720) else \
+        synth.road_scaled(W_, H_, seed=2 + rank)
     left_np, right_np = synth.render(sc)
     model = B.RoadModel.make(*synth.true_model(sc))
     params = B.default_params()

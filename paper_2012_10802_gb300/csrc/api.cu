@@ -202,6 +202,7 @@ size_t transform_scratch_bytes(int W, int H) {
   carve_size<int64_t>(acc, 46);
   carve_size<pd_road_model>(acc, 1);
   carve_size<RoadCoefF>(acc, 1);
+  carve_size<uint8_t>(acc, roll_scratch_bytes());
   return acc;
 }
 
@@ -212,11 +213,12 @@ pd_status transform_enqueue(pd_ctx* ctx, const float* D1, int W, int H, int orde
   int64_t* sums = c.take<int64_t>(46);
   pd_road_model* fit = c.take<pd_road_model>(1);
   RoadCoefF* coef = c.take<RoadCoefF>(1);
+  double* grid = reinterpret_cast<double*>(c.take<uint8_t>(roll_scratch_bytes()));
   cudaStream_t s = ctx->stream;
   launch_moments(s, D1, W, H, part, sums);
-  launch_roll_solve(s, sums, order, W, H, fitted ? fitted : fit, coef);
+  int n = launch_roll_solve(s, sums, order, W, H, fitted ? fitted : fit, coef, grid);
   launch_d2(s, D1, W, H, coef, delta_dt, D2);
-  count_launches(ctx, 4);
+  count_launches(ctx, 3 + n);
   return launched(ctx, "pd_transform");
 }
 

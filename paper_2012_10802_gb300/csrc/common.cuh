@@ -79,8 +79,8 @@ void launch_warp(cudaStream_t s, const uint8_t* right, int W, int H, size_t pitc
 void launch_census(cudaStream_t s, const uint8_t* img, int W, int H, size_t pitch,
                    const int32_t* kappa, uint32_t* codes);
 // layout 0: natural [H][W][D]; layout 1: the interleaved layout of the aggregation kernels
-// (D % 32 == 0): within each 32-disparity group g, byte 2j holds d = 32g + j and byte 2j+1 holds
-// d = 32g + 16 + j.
+// (D % 16 == 0): within each 16-disparity group g, byte 2j holds d = 16g + j and byte 2j+1 holds
+// d = 16g + 8 + j.
 void launch_cost(cudaStream_t s, const uint32_t* cl, const uint32_t* cr, int W, int H, int D,
                  int layout, uint8_t* cost);
 void launch_to_interleaved(cudaStream_t s, const uint8_t* natural, size_t n_pix, int D,
@@ -108,8 +108,10 @@ struct RoadCoefF {
 };
 size_t moments_scratch_bytes(int W, int H);
 void launch_moments(cudaStream_t s, const float* D1, int W, int H, void* scratch, int64_t* sums);
-void launch_roll_solve(cudaStream_t s, const int64_t* sums, int order, int W, int H,
-                       pd_road_model* fitted, RoadCoefF* coef);
+size_t roll_scratch_bytes();
+// Returns the number of kernels launched.
+int launch_roll_solve(cudaStream_t s, const int64_t* sums, int order, int W, int H,
+                      pd_road_model* fitted, RoadCoefF* coef, double* grid_scratch);
 void launch_d2(cudaStream_t s, const float* D1, int W, int H, const RoadCoefF* coef,
                float delta_dt, float* D2);
 

@@ -26,6 +26,35 @@ __device__ float slic_gradient(const float* __restrict__ D2, int W, int H, int x
   return gx * gx + gy * gy;
 }
 
+// Sums (count, x, y, q) over the lanes that share a label, one representative lane per label
+// adding them into shared slots (slot >= 0) or straight into the global sums (slot < 0).  All 32
+// lanes must call it; lanes with valid == false contribute nothing.  q is summed exactly in two
+// 16-bit halves.
+__device__ void warp_accumulate(bool valid, int lab, int slot, int x, int y, long long q,
+                                unsigned long long (*sacc)[4], unsigned long long* acc) {
+  const int lane = threadIdx.x & 31;
+  unsigned pending = __ballot_sync(0xffffffffu, valid);
+  while (pending) {
+    const int leader = __ffs(pending) - 1;
+    const int lab_l = __shfl_sync(0xffffffffu, lab, leader);
+    const bool mine = valid && lab == lab_l;
+    const unsigned peers = __ballot_sync(0xffffffffu, mine);
+    const int xs = __reduce_add_sync(0xffffffffu, mine ? x : 0);
+    const int ys = __reduce_add_sync(0xffffffffu, mine ? y : 0);
+    const unsigned qlo = __reduce_add_sync(0xffffffffu, mine ? (unsigned)(q & 0xffff) : 0u);
+    const int qhi = __reduce_add_sync(0xffffffffu, mine ? (int)(q >> 16) : 0);
+    if (lane == leader) {
+      const long long qs = (long long)qhi * 65536LL + (long long)qlo;
+      unsigned long long* a = slot >= 0 ? sacc[slot] : acc + 4 * (size_t)lab;
+      atomicAdd(a + 0, (unsigned long long)__popc(peers));
+      atomicAdd(a + 1, (unsigned long long)xs);
+      atomicAdd(a + 2, (unsigned long long)ys);
+      atomicAdd(a + 3, (unsigned long long)qs);
+    }
+    pending &= ~peers;
+  }
+}
+
 // Grid seeds moved to the lowest-gradient pixel of their 3x3 neighbourhood (seed wins ties).
 __global__ void k_slic_seeds(const float* __restrict__ D2, int W, int H, int nx, int ny,
                              float* __restrict__ cx, float* __restrict__ cy,
@@ -116,11 +145,13 @@ __global__ void __launch_bounds__(kTileThreads) k_slic_assign(
   __syncthreads();
 
   const int x = x0 + (tid % kTile), y = y0 + (tid / kTile);
-  if (x < W && y < H) {
+  const bool inside = x < W && y < H;
+  int lab = -1, slot = -1;
+  long long q = 0;
+  if (inside) {
     const size_t p = (size_t)y * W + x;
     const float val = D2[p];
-    int lab = labels[p];
-    int slot = -1;
+    lab = labels[p];
     if (do_assign) {
       float best = INFINITY;
       const float fxp = (float)x, fyp = (float)y;
@@ -152,20 +183,12 @@ __global__ void __launch_bounds__(kTileThreads) k_slic_assign(
       }
       labels[p] = lab;
     }
-    long long q = __double2ll_rn((double)val * 1024.0);
-    if (slot >= 0) {
-      atomicAdd(&sacc[slot][0], 1ULL);
-      atomicAdd(&sacc[slot][1], (unsigned long long)x);
-      atomicAdd(&sacc[slot][2], (unsigned long long)y);
-      atomicAdd(&sacc[slot][3], (unsigned long long)q);
-    } else {
-      unsigned long long* a = acc + 4 * (size_t)lab;
-      atomicAdd(a + 0, 1ULL);
-      atomicAdd(a + 1, (unsigned long long)x);
-      atomicAdd(a + 2, (unsigned long long)y);
-      atomicAdd(a + 3, (unsigned long long)q);
-    }
+    q = __double2ll_rn((double)val * 1024.0);
   }
+  // a label's slot is the same for every lane that has it, so grouping by label groups by slot;
+  // lanes that kept an uncovered pixel's old label (slot -1) go straight to the global sums
+  warp_accumulate(inside && slot >= 0, lab, slot, x, y, q, sacc, acc);
+  warp_accumulate(inside && slot < 0, lab, -1, x, y, q, sacc, acc);
   __syncthreads();
   if (!overflow)
     for (int i = tid; i < nc; i += kTileThreads) {
@@ -216,41 +239,67 @@ constexpr int kBins = 257;  // k = 0..255 plus an overflow bin for everything at
 // with exact sums n, sum a, sum b, sum a^2 + b^2, over interior pixels with a valid 3x3 window;
 // a = rint(1024 D2(p)), b = sum of rint(1024 D2) over the 8 neighbours.  Region 1 of threshold
 // k/8 is {kmax < k}, region 2 is {kmin >= k}.
-__global__ void k_thresh_hist(const float* __restrict__ D2, const float* __restrict__ D1, int W,
-                              int H, unsigned long long* __restrict__ hist /* [2][kBins][4] */) {
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Adds (1, a, b, a^2 + b^2) of the lanes sharing a bin into the shared histogram h, one lane per
+// distinct bin.  All 32 lanes must call it.
+__device__ void warp_hist(bool valid, int bin, long long a, long long b,
+                          unsigned long long (*h)[4]) {
+  const int lane = threadIdx.x & 31;
+  unsigned pending = __ballot_sync(0xffffffffu, valid);
+  while (pending) {
+    const int leader = __ffs(pending) - 1;
+    const int bl = __shfl_sync(0xffffffffu, bin, leader);
+    const bool mine = valid && bin == bl;
+    const unsigned peers = __ballot_sync(0xffffffffu, mine);
+    const long long sa = warp_sum_ll(mine ? a : 0);
+    const long long sb = warp_sum_ll(mine ? b : 0);
+    const long long sq = warp_sum_ll(mine ? a * a + b * b : 0);
+    if (lane == leader) {
+      atomicAdd(&h[bl][0], (unsigned long long)__popc(peers));
+      atomicAdd(&h[bl][1], (unsigned long long)sa);
+      atomicAdd(&h[bl][2], (unsigned long long)sb);
+      atomicAdd(&h[bl][3], (unsigned long long)sq);
+    }
+    pending &= ~peers;
+  }
+}
+
+// Histograms of kmax = max(floor(a / 128), floor(b / 1024)) and kmin (the same with min), each
+// with exact sums n, sum a, sum b, sum a^2 + b^2, over interior pixels with a valid 3x3 window;
+// a = rint(1024 D2(p)), b = sum of rint(1024 D2) over the 8 neighbours.  Region 1 of threshold
+// k/8 is {kmax < k}, region 2 is {kmin >= k}.  Blocks stride over rows.
+__global__ void __launch_bounds__(256) k_thresh_hist(const float* __restrict__ D2,
+                                                     const float* __restrict__ D1, int W, int H,
+                                                     unsigned long long* __restrict__ hist) {
   __shared__ unsigned long long sh[2][kBins][4];
   for (int i = threadIdx.x; i < 2 * kBins * 4; i += blockDim.x) (&sh[0][0][0])[i] = 0ULL;
   __syncthreads();
-  int u = blockIdx.x * blockDim.x + threadIdx.x;
-  int v = blockIdx.y;
-  if (u >= 1 && u < W - 1 && v >= 1 && v < H - 1) {
-    bool ok = true;
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int v = blockIdx.y; v < H; v += gridDim.y) {
+    bool ok = u >= 1 && u < W - 1 && v >= 1 && v < H - 1;
     long long a = 0, b = 0;
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        size_t q = (size_t)(v + dy) * W + (u + dx);
-        if (!(D1[q] >= 0.0f)) ok = false;
-        long long qq = __double2ll_rn((double)D2[q] * 1024.0);
-        if (dx == 0 && dy == 0)
-          a = qq;
-        else
-          b += qq;
-      }
     if (ok) {
-      long long ka = a >> 7, kb = b >> 10;
-      long long kmax = ka > kb ? ka : kb, kmin = ka < kb ? ka : kb;
-      int imax = (int)(kmax < 0 ? 0 : (kmax > 256 ? 256 : kmax));
-      int imin = (int)(kmin < 0 ? 0 : (kmin > 256 ? 256 : kmin));
-      unsigned long long sq = (unsigned long long)(a * a) + (unsigned long long)(b * b);
-      atomicAdd(&sh[0][imax][0], 1ULL);
-      atomicAdd(&sh[0][imax][1], (unsigned long long)a);
-      atomicAdd(&sh[0][imax][2], (unsigned long long)b);
-      atomicAdd(&sh[0][imax][3], sq);
-      atomicAdd(&sh[1][imin][0], 1ULL);
-      atomicAdd(&sh[1][imin][1], (unsigned long long)a);
-      atomicAdd(&sh[1][imin][2], (unsigned long long)b);
-      atomicAdd(&sh[1][imin][3], sq);
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          size_t q = (size_t)(v + dy) * W + (u + dx);
+          if (!(D1[q] >= 0.0f)) ok = false;
+          long long qq = __double2ll_rn((double)D2[q] * 1024.0);
+          if (dx == 0 && dy == 0)
+            a = qq;
+          else
+            b += qq;
+        }
     }
+    long long ka = a >> 7, kb = b >> 10;
+    long long kmax = ka > kb ? ka : kb, kmin = ka < kb ? ka : kb;
+    int imax = (int)(kmax < 0 ? 0 : (kmax > 256 ? 256 : kmax));
+    int imin = (int)(kmin < 0 ? 0 : (kmin > 256 ? 256 : kmin));
+    warp_hist(ok, imax, a, b, sh[0]);
+    warp_hist(ok, imin, a, b, sh[1]);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < 2 * kBins * 4; i += blockDim.x) {
@@ -259,56 +308,71 @@ __global__ void k_thresh_hist(const float* __restrict__ D2, const float* __restr
   }
 }
 
-// E2(t) of Eq. (17) for t = k/8, k = 1..255, from prefix (region 1) and suffix (region 2) sums;
-// t_r = smallest minimiser; t_s from mode.  One thread, 255 steps.
-__global__ void k_thresh_solve(const unsigned long long* __restrict__ hist, float delta_pd,
-                               int mode, double* __restrict__ thr, double* __restrict__ E2) {
-  if (threadIdx.x != 0) return;
-  const unsigned long long(*hmax)[4] = reinterpret_cast<const unsigned long long(*)[4]>(hist);
-  const unsigned long long(*hmin)[4] = reinterpret_cast<const unsigned long long(*)[4]>(hist + kBins * 4);
-  long long n2 = 0, a2 = 0, b2 = 0;
-  unsigned long long s2 = 0;
-  for (int j = 1; j < kBins; ++j) {  // region 2 at k = 1: kmin >= 1
-    n2 += (long long)hmin[j][0];
-    a2 += (long long)hmin[j][1];
-    b2 += (long long)hmin[j][2];
-    s2 += hmin[j][3];
-  }
-  long long n1 = (long long)hmax[0][0], a1 = (long long)hmax[0][1], b1 = (long long)hmax[0][2];
-  unsigned long long s1 = hmax[0][3];
-  int best = -1;
-  double bestE = 0.0, bestMean = 0.0;
-  if (E2) E2[0] = NAN;
-  for (int k = 1; k < 256; ++k) {
-    double e = NAN;
+// E2(t) of Eq. (17) for t = k/8, k = 1..255: thread k forms the region sums from the histograms
+// (region 1: kmax bins below k, region 2: kmin bins from k up), evaluates E2 in double, and the
+// block takes the smallest minimising k; t_s from mode.
+constexpr int kSolveThreads = 256;
+
+__global__ void __launch_bounds__(kSolveThreads) k_thresh_solve(
+    const unsigned long long* __restrict__ hist, float delta_pd, int mode,
+    double* __restrict__ thr, double* __restrict__ E2) {
+  __shared__ unsigned long long sh[2][kBins][4];
+  __shared__ double sE[kSolveThreads];
+  __shared__ int sK[kSolveThreads];
+  __shared__ double sMean[kSolveThreads];
+  for (int i = threadIdx.x; i < 2 * kBins * 4; i += kSolveThreads) (&sh[0][0][0])[i] = hist[i];
+  __syncthreads();
+  const int k = threadIdx.x;
+  double e = NAN, mean = 0.0;
+  if (k >= 1 && k < 256) {
+    long long n1 = 0, a1 = 0, b1 = 0, n2 = 0, a2 = 0, b2 = 0;
+    unsigned long long s1 = 0, s2 = 0;
+    for (int j = 0; j < k; ++j) {
+      n1 += (long long)sh[0][j][0];
+      a1 += (long long)sh[0][j][1];
+      b1 += (long long)sh[0][j][2];
+      s1 += sh[0][j][3];
+    }
+    for (int j = k; j < kBins; ++j) {
+      n2 += (long long)sh[1][j][0];
+      a2 += (long long)sh[1][j][1];
+      b2 += (long long)sh[1][j][2];
+      s2 += sh[1][j][3];
+    }
     if (n1 != 0 && n2 != 0) {
       double e1 = (double)s1 - ((double)a1 * (double)a1 + (double)b1 * (double)b1) / (double)n1;
       double e2 = (double)s2 - ((double)a2 * (double)a2 + (double)b2 * (double)b2) / (double)n2;
       e = e1 + e2;
-      if (best < 0 || e < bestE) {
-        best = k;
-        bestE = e;
-        bestMean = ((double)a2 / (double)n2) / 1024.0;
+      mean = ((double)a2 / (double)n2) / 1024.0;
+    }
+  }
+  if (E2 && k < 256) E2[k] = e;
+  // block argmin over the non-NaN energies, smallest k on ties
+  sE[k] = e;
+  sK[k] = k;
+  sMean[k] = mean;
+  __syncthreads();
+  for (int s = kSolveThreads / 2; s > 0; s >>= 1) {
+    if (k < s) {
+      double eo = sE[k + s], em = sE[k];
+      int ko = sK[k + s], km = sK[k];
+      bool take = !isnan(eo) && (isnan(em) || eo < em || (eo == em && ko < km));
+      if (take) {
+        sE[k] = eo;
+        sK[k] = ko;
+        sMean[k] = sMean[k + s];
       }
     }
-    if (E2) E2[k] = e;
-    // move to k + 1: region 1 gains bin k of kmax, region 2 loses bin k of kmin
-    n1 += (long long)hmax[k][0];
-    a1 += (long long)hmax[k][1];
-    b1 += (long long)hmax[k][2];
-    s1 += hmax[k][3];
-    n2 -= (long long)hmin[k][0];
-    a2 -= (long long)hmin[k][1];
-    b2 -= (long long)hmin[k][2];
-    s2 -= hmin[k][3];
+    __syncthreads();
   }
-  if (best < 0) {
+  if (k != 0) return;
+  if (isnan(sE[0])) {
     thr[0] = NAN;
     thr[1] = -INFINITY;
     return;
   }
-  thr[0] = (double)best * 0.125;
-  thr[1] = (mode == 0 ? bestMean : thr[0]) - (double)delta_pd;
+  thr[0] = (double)sK[0] * 0.125;
+  thr[1] = (mode == 0 ? sMean[0] : thr[0]) - (double)delta_pd;
 }
 
 __global__ void k_mask(const float* __restrict__ D3, size_t N, const double* __restrict__ thr,
@@ -382,8 +446,11 @@ void launch_threshold(cudaStream_t s, const float* D2, const float* D1, const fl
   double* thr = c.take<double>(2);
   if (thresholds) thr = thresholds;
   cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * 2 * kBins * 4, s);
-  k_thresh_hist<<<dim3((W + 255) / 256, H), 256, 0, s>>>(D2, D1, W, H, hist);
-  k_thresh_solve<<<1, 32, 0, s>>>(hist, delta_pd, mode, thr, E2);
+  const int xb = (W + 255) / 256;
+  int yb = (2 * 152 + xb - 1) / xb;
+  yb = yb < H ? yb : H;
+  k_thresh_hist<<<dim3(xb, yb), 256, 0, s>>>(D2, D1, W, H, hist);
+  k_thresh_solve<<<1, kSolveThreads, 0, s>>>(hist, delta_pd, mode, thr, E2);
   size_t N = (size_t)W * H;
   k_mask<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(D3, N, thr, mask);
 }

@@ -1,5 +1,6 @@
 // Sec. II-C on the GPU: exact moment sums of the road disparities, the roll / road-model fit of
-// Eqs. (11)-(12) in one thread block (no host round trip), and the Eq. (13) transformation.
+// Eqs. (11)-(12) on the device (a grid of angles over many SMs, then one refining block; no host
+// round trip), and the Eq. (13) transformation.
 #include "common.cuh"
 
 namespace pd {
@@ -7,7 +8,7 @@ namespace pd {
 namespace {
 
 constexpr int kMomThreads = 256;
-constexpr int kMomPixPerBlock = 16384;  // keeps every per-block int64 partial exact (W, H <= 4096)
+constexpr int kMomPixPerBlock = 2048;  // keeps every per-block int64 partial exact (W, H <= 4096)
 constexpr int kNumSums = 23;
 
 __device__ __forceinline__ long long warp_sum_ll(long long x) {
@@ -66,15 +67,21 @@ __global__ void __launch_bounds__(kMomThreads) k_moments_partial(const float* __
   }
 }
 
-// Sums the block partials exactly in 128 bits; writes (low, high) 64-bit pairs.
+// Sums the block partials exactly in 128 bits; writes (low, high) 64-bit pairs.  One warp per sum.
 __global__ void k_moments_final(const long long* __restrict__ partial, int nblocks,
                                 int64_t* __restrict__ sums) {
-  int i = threadIdx.x;
-  if (i >= kNumSums) return;
+  __shared__ __int128 red[kNumSums][32];
+  const int i = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __int128 s = 0;
-  for (int b = 0; b < nblocks; ++b) s += (__int128)partial[(size_t)b * kNumSums + i];
-  sums[2 * i] = (int64_t)(unsigned long long)s;
-  sums[2 * i + 1] = (int64_t)(s >> 64);
+  for (int b = lane; b < nblocks; b += 32) s += (__int128)partial[(size_t)b * kNumSums + i];
+  red[i][lane] = s;
+  __syncwarp();
+  if (lane == 0) {
+    __int128 t = 0;
+    for (int l = 0; l < 32; ++l) t += red[i][l];
+    sums[2 * i] = (int64_t)(unsigned long long)t;
+    sums[2 * i + 1] = (int64_t)(t >> 64);
+  }
 }
 
 // Correctly rounded conversion of a signed 128-bit integer (lo, hi) to double: the top 64
@@ -177,38 +184,82 @@ __device__ double e0min_d(const MomD& M, int order, double sc, double phi, doubl
   return dd - fit;
 }
 
-constexpr int kRollThreads = 256;
 constexpr int kGridN = 3001;
 constexpr double kGridStep = 1.7453292519943295e-04;  // 0.01 degree
+constexpr int kGridThreads = 128;
+constexpr int kRefineThreads = 128;
 
-// One block: reads the exact sums, finds phi (closed form for order 1; 0.01-degree grid over
-// +-15 degrees and golden-section refinement for order 2), solves Eq. (11) for the coefficients,
-// and writes the model plus its float coefficients for the transform kernel.
-__global__ void __launch_bounds__(kRollThreads) k_roll_solve(const int64_t* __restrict__ sums,
-                                                             int order, int W, int H,
-                                                             pd_road_model* fitted,
-                                                             RoadCoefF* coef) {
-  __shared__ MomD M;
-  __shared__ double sE[kRollThreads];
-  __shared__ int sK[kRollThreads];
-  if (threadIdx.x == 0) {
-    int k = 1;  // skip the count; m[0][0] is the same number
-    for (int i = 0; i <= 4; ++i)
-      for (int j = 0; i + j <= 4; ++j, ++k)
-        M.m[i][j] = i128_to_double((unsigned long long)sums[2 * k], (long long)sums[2 * k + 1]);
-    for (int i = 0; i <= 2; ++i)
-      for (int j = 0; i + j <= 2; ++j, ++k)
-        M.q[i][j] = i128_to_double((unsigned long long)sums[2 * k], (long long)sums[2 * k + 1]);
-    M.qq = i128_to_double((unsigned long long)sums[2 * k], (long long)sums[2 * k + 1]);
-  }
-  __syncthreads();
+__device__ void load_moments(const int64_t* __restrict__ sums, MomD& M) {
+  int k = 1;  // skip the count; m[0][0] is the same number
+  for (int i = 0; i <= 4; ++i)
+    for (int j = 0; i + j <= 4; ++j, ++k)
+      M.m[i][j] = i128_to_double((unsigned long long)sums[2 * k], (long long)sums[2 * k + 1]);
+  for (int i = 0; i <= 2; ++i)
+    for (int j = 0; i + j <= 2; ++j, ++k)
+      M.q[i][j] = i128_to_double((unsigned long long)sums[2 * k], (long long)sums[2 * k + 1]);
+  M.qq = i128_to_double((unsigned long long)sums[2 * k], (long long)sums[2 * k + 1]);
+}
+
+__device__ double coord_scale_d(int W, int H) {
   int mmax = W > H ? W : H;
   double sc = 1.0;
   while (sc < (double)mmax) sc *= 2.0;
+  return sc;
+}
+
+// E0min on the 0.01-degree grid over +-15 degrees, one angle per thread across many SMs.
+__global__ void __launch_bounds__(kGridThreads) k_roll_grid(const int64_t* __restrict__ sums,
+                                                            int order, int W, int H,
+                                                            double* __restrict__ E) {
+  __shared__ MomD M;
+  if (threadIdx.x == 0) load_moments(sums, M);
+  __syncthreads();
+  int k = blockIdx.x * kGridThreads + threadIdx.x;
+  if (k >= kGridN) return;
   double beta[3];
-  double phi = 0.0;
+  E[k] = e0min_d(M, order, coord_scale_d(W, H), (double)(k - kGridN / 2) * kGridStep, beta);
+}
+
+// Block argmin of (value, index), smallest index on ties.  Returns the winner to every thread.
+__device__ void block_argmin(double e, int k, double* sE, int* sK, double& be, int& bk) {
+  sE[threadIdx.x] = e;
+  sK[threadIdx.x] = k;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      double eo = sE[threadIdx.x + s];
+      int ko = sK[threadIdx.x + s];
+      if (eo < sE[threadIdx.x] || (eo == sE[threadIdx.x] && ko < sK[threadIdx.x])) {
+        sE[threadIdx.x] = eo;
+        sK[threadIdx.x] = ko;
+      }
+    }
+    __syncthreads();
+  }
+  be = sE[0];
+  bk = sK[0];
+  __syncthreads();
+}
+
+// Refines the roll (order 2: around the best grid angle, by rounds of kRefineThreads angles that
+// shrink the bracket about 64x each, to below 1e-12 rad; order 1: the least-squares plane in
+// closed form), solves Eq. (11) for the coefficients and writes the model and its float form.
+__global__ void __launch_bounds__(kRefineThreads) k_roll_refine(const int64_t* __restrict__ sums,
+                                                                const double* __restrict__ E,
+                                                                int order, int W, int H,
+                                                                pd_road_model* fitted,
+                                                                RoadCoefF* coef) {
+  __shared__ MomD M;
+  __shared__ double sE[kRefineThreads];
+  __shared__ int sK[kRefineThreads];
+  __shared__ double sPhi;
+  if (threadIdx.x == 0) load_moments(sums, M);
+  __syncthreads();
+  const double sc = coord_scale_d(W, H);
+  double beta[3];
   if (order == 1) {
     if (threadIdx.x == 0) {
+      double phi = 0.0;
       double s1 = sc, s2 = sc * sc;
       double A[3][3] = {{M.m[0][0], M.m[0][1] / s1, M.m[1][0] / s1},
                         {M.m[0][1] / s1, M.m[0][2] / s2, M.m[1][1] / s2},
@@ -216,60 +267,42 @@ __global__ void __launch_bounds__(kRollThreads) k_roll_solve(const int64_t* __re
       double b[3] = {M.q[0][0] / 1024.0, M.q[0][1] / s1 / 1024.0, M.q[1][0] / s1 / 1024.0};
       double x[3] = {0, 0, 0};
       if (spd_solve_d(3, A, b, x) == 0 && x[1] != 0.0) phi = atan(-x[2] / x[1]);
+      sPhi = phi;
     }
   } else {
-    double bestE = INFINITY;
-    int bestK = kGridN;
-    for (int k = threadIdx.x; k < kGridN; k += kRollThreads) {
-      double e = e0min_d(M, order, sc, (double)(k - kGridN / 2) * kGridStep, beta);
-      if (e < bestE) {
-        bestE = e;
-        bestK = k;
+    double be = INFINITY;
+    int bk = kGridN;
+    for (int k = threadIdx.x; k < kGridN; k += kRefineThreads) {
+      double e = E[k];
+      if (e < be) {
+        be = e;
+        bk = k;
       }
     }
-    sE[threadIdx.x] = bestE;
-    sK[threadIdx.x] = bestK;
-    __syncthreads();
-    for (int s = kRollThreads / 2; s > 0; s >>= 1) {
-      if (threadIdx.x < s) {
-        double eo = sE[threadIdx.x + s];
-        int ko = sK[threadIdx.x + s];
-        if (eo < sE[threadIdx.x] || (eo == sE[threadIdx.x] && ko < sK[threadIdx.x])) {
-          sE[threadIdx.x] = eo;
-          sK[threadIdx.x] = ko;
-        }
-      }
-      __syncthreads();
+    block_argmin(be, bk, sE, sK, be, bk);
+    int best = bk < kGridN ? bk : 0;
+    int klo = best > 0 ? best - 1 : 0;
+    int khi = best < kGridN - 1 ? best + 1 : kGridN - 1;
+    double a = (double)(klo - kGridN / 2) * kGridStep;
+    double b = (double)(khi - kGridN / 2) * kGridStep;
+    double phi = 0.5 * (a + b);
+    for (int round = 0; round < 12 && (b - a) > 1e-12; ++round) {
+      const double h = (b - a) / (double)(kRefineThreads + 1);
+      double x = a + h * (double)(threadIdx.x + 1);
+      double e = e0min_d(M, order, sc, x, beta);
+      int t;
+      block_argmin(e, threadIdx.x, sE, sK, e, t);
+      phi = a + h * (double)(t + 1);
+      double na = a + h * (double)t;
+      double nb = a + h * (double)(t + 2);
+      a = na;
+      b = nb;
     }
-    if (threadIdx.x == 0) {
-      int best = sK[0] < kGridN ? sK[0] : 0;
-      int klo = best > 0 ? best - 1 : 0;
-      int khi = best < kGridN - 1 ? best + 1 : kGridN - 1;
-      double a = (double)(klo - kGridN / 2) * kGridStep;
-      double b = (double)(khi - kGridN / 2) * kGridStep;
-      const double g = 0.6180339887498949;
-      double x1 = b - g * (b - a), x2 = a + g * (b - a);
-      double f1 = e0min_d(M, order, sc, x1, beta);
-      double f2 = e0min_d(M, order, sc, x2, beta);
-      for (int it = 0; it < 200 && (b - a) > 1e-12; ++it) {
-        if (f1 <= f2) {
-          b = x2;
-          x2 = x1;
-          f2 = f1;
-          x1 = b - g * (b - a);
-          f1 = e0min_d(M, order, sc, x1, beta);
-        } else {
-          a = x1;
-          x1 = x2;
-          f1 = f2;
-          x2 = a + g * (b - a);
-          f2 = e0min_d(M, order, sc, x2, beta);
-        }
-      }
-      phi = 0.5 * (a + b);
-    }
+    if (threadIdx.x == 0) sPhi = phi;
   }
+  __syncthreads();
   if (threadIdx.x != 0) return;
+  const double phi = sPhi;
   e0min_d(M, order, sc, phi, beta);
   double k = 2.0 / sc;
   double vc = (double)(H - 1) * 0.5;
@@ -321,16 +354,25 @@ size_t moments_scratch_bytes(int W, int H) {
   return n * kNumSums * sizeof(long long);
 }
 
+size_t roll_scratch_bytes() { return kGridN * sizeof(double); }
+
 void launch_moments(cudaStream_t s, const float* D1, int W, int H, void* scratch, int64_t* sums) {
   int nblocks = (int)(((size_t)W * H + kMomPixPerBlock - 1) / kMomPixPerBlock);
   long long* partial = static_cast<long long*>(scratch);
   k_moments_partial<<<nblocks, kMomThreads, 0, s>>>(D1, W, H, partial);
-  k_moments_final<<<1, 32, 0, s>>>(partial, nblocks, sums);
+  k_moments_final<<<1, kNumSums * 32, 0, s>>>(partial, nblocks, sums);
 }
 
-void launch_roll_solve(cudaStream_t s, const int64_t* sums, int order, int W, int H,
-                       pd_road_model* fitted, RoadCoefF* coef) {
-  k_roll_solve<<<1, kRollThreads, 0, s>>>(sums, order, W, H, fitted, coef);
+int launch_roll_solve(cudaStream_t s, const int64_t* sums, int order, int W, int H,
+                      pd_road_model* fitted, RoadCoefF* coef, double* grid_scratch) {
+  int n = 1;
+  if (order == 2) {
+    k_roll_grid<<<(kGridN + kGridThreads - 1) / kGridThreads, kGridThreads, 0, s>>>(
+        sums, order, W, H, grid_scratch);
+    ++n;
+  }
+  k_roll_refine<<<1, kRefineThreads, 0, s>>>(sums, grid_scratch, order, W, H, fitted, coef);
+  return n;
 }
 
 void launch_d2(cudaStream_t s, const float* D1, int W, int H, const RoadCoefF* coef,

@@ -2,13 +2,13 @@
 // Eq. (8) aggregation, Eq. (9) winner-take-all with sub-pixel step and left-right check, Eq. (10).
 //
 // Aggregation design: every path of every direction is an independent dynamic-programming line.
-// A line is owned by G = D/32 lanes of a warp; each lane keeps 32 disparities as 16 packed
-// u16x2 words, word j holding (d = 32g + j, d = 32g + 16 + j).  With that pairing the d-1 / d+1
+// A line is owned by G = D/16 lanes of a warp; each lane keeps 16 disparities as 8 packed u16x2
+// words, word j holding (d = 16g + j, d = 16g + 8 + j).  With that pairing the d-1 / d+1
 // neighbours of word j are words j-1 / j+1, so the recurrence needs no byte shuffling: per word it
 // is one 3-input min, one fused add-min and one add (Hopper/Blackwell DPX instructions), and only
 // the two ends of a lane's range cross lanes.  The matching cost is computed once per (p, d) into
-// a uint8 volume (popcount is a quarter-rate instruction) and every direction reads it with 16-byte
-// loads.
+// a uint8 volume (popcount is a quarter-rate instruction) and every direction reads it with one
+// 16-byte load per lane and step, issued kPrefetch steps ahead from a register ring.
 #include <cstdio>
 
 #include "common.cuh"
@@ -89,14 +89,14 @@ __global__ void k_census(const uint8_t* __restrict__ img, int W, int H, size_t p
 }
 
 // ----------------------------------------------------------------------------- cost
-// Interleaved layout, D % 32 == 0: one thread per (pixel, 32-disparity group), 32 bytes out.
+// Interleaved layout, D % 16 == 0: one thread per (pixel, 16-disparity group), 16 bytes out.
 constexpr int kCostThreads = 256;
 
 __global__ void __launch_bounds__(kCostThreads) k_cost_il(const uint32_t* __restrict__ cl,
                                                           const uint32_t* __restrict__ cr, int W,
                                                           int D, uint8_t* __restrict__ cost) {
   __shared__ uint32_t sR[kCostThreads + kMaxD];
-  const int groups = D >> 5;
+  const int groups = D >> 4;
   const int P = kCostThreads / groups;  // pixels per block
   const int v = blockIdx.y;
   const int u0 = blockIdx.x * P;
@@ -110,23 +110,21 @@ __global__ void __launch_bounds__(kCostThreads) k_cost_il(const uint32_t* __rest
   const int g = threadIdx.x % groups;
   if (u >= W) return;
   const uint32_t c0 = cl[(size_t)v * W + u];
-  uint32_t w[8];
+  uint32_t w[4];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
+  for (int i = 0; i < 4; ++i) {
     uint32_t packed = 0;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       int p = 4 * i + b;
-      int d = 32 * g + (p >> 1) + ((p & 1) << 4);
+      int d = 16 * g + (p >> 1) + ((p & 1) << 3);
       int x = u - d;
       uint32_t c = x >= 0 ? (uint32_t)__popc(c0 ^ sR[x - base]) : (uint32_t)kCensusBits;
       packed |= c << (8 * b);
     }
     w[i] = packed;
   }
-  uint4* dst = reinterpret_cast<uint4*>(cost + ((size_t)v * W + u) * D + 32 * g);
-  dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
-  dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+  *reinterpret_cast<uint4*>(cost + ((size_t)v * W + u) * D + 16 * g) = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
 // Natural layout, any 1 <= D <= 256: one thread per (pixel, d).
@@ -155,39 +153,33 @@ __global__ void __launch_bounds__(kCostThreads) k_cost_nat(const uint32_t* __res
   cost[row0 + idx] = c;
 }
 
-// Natural <-> interleaved byte order within each 32-disparity group.
+// Natural <-> interleaved byte order within each 16-disparity group.
 __global__ void k_to_interleaved(const uint8_t* __restrict__ in, size_t n_groups,
                                  uint8_t* __restrict__ out) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_groups) return;
-  const uint4* s = reinterpret_cast<const uint4*>(in + 32 * t);
-  uint4 a = s[0], b = s[1];
-  uint32_t n[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-  uint32_t o[8];
+  uint4 a = reinterpret_cast<const uint4*>(in)[t];
+  uint32_t n[4] = {a.x, a.y, a.z, a.w};
+  uint32_t o[4];
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
-    o[i] = __byte_perm(n[i >> 1], n[4 + (i >> 1)], (i & 1) ? 0x7362 : 0x5140);
-  uint4* d = reinterpret_cast<uint4*>(out + 32 * t);
-  d[0] = make_uint4(o[0], o[1], o[2], o[3]);
-  d[1] = make_uint4(o[4], o[5], o[6], o[7]);
+  for (int i = 0; i < 4; ++i)
+    o[i] = __byte_perm(n[i >> 1], n[2 + (i >> 1)], (i & 1) ? 0x7362 : 0x5140);
+  reinterpret_cast<uint4*>(out)[t] = make_uint4(o[0], o[1], o[2], o[3]);
 }
 
 __global__ void k_to_natural(const uint8_t* __restrict__ in, size_t n_groups,
                              uint8_t* __restrict__ out) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_groups) return;
-  const uint4* s = reinterpret_cast<const uint4*>(in + 32 * t);
-  uint4 a = s[0], b = s[1];
-  uint32_t r[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-  uint32_t o[8];
+  uint4 a = reinterpret_cast<const uint4*>(in)[t];
+  uint32_t r[4] = {a.x, a.y, a.z, a.w};
+  uint32_t o[4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 2; ++i) {
     o[i] = __byte_perm(r[2 * i], r[2 * i + 1], 0x6420);
-    o[4 + i] = __byte_perm(r[2 * i], r[2 * i + 1], 0x7531);
+    o[2 + i] = __byte_perm(r[2 * i], r[2 * i + 1], 0x7531);
   }
-  uint4* d = reinterpret_cast<uint4*>(out + 32 * t);
-  d[0] = make_uint4(o[0], o[1], o[2], o[3]);
-  d[1] = make_uint4(o[4], o[5], o[6], o[7]);
+  reinterpret_cast<uint4*>(out)[t] = make_uint4(o[0], o[1], o[2], o[3]);
 }
 
 // ----------------------------------------------------------------------------- Eq. (8)
@@ -209,6 +201,8 @@ __device__ __forceinline__ void line_pixel(const LineGeom& L, int W, int H, int 
     act = line < L.nlines && u >= 0 && u < W;
   }
 }
+
+constexpr int kPrefetch = 8;  // cost loads in flight per lane (steps ahead)
 
 template <int G>
 __global__ void __launch_bounds__(kAggWarps * 32) k_aggregate(const uint8_t* __restrict__ cost,
@@ -249,116 +243,113 @@ __global__ void __launch_bounds__(kAggWarps * 32) k_aggregate(const uint8_t* __r
     L.nsteps = L.vhi - L.vlo + 1;
   }
   uint8_t* dst_vol = out + (size_t)r * vol_bytes;
+  const uint8_t* csrc = cost + 16 * g;
 
-  uint32_t N[16];
+  uint32_t N[8];
 #pragma unroll
-  for (int j = 0; j < 16; ++j) N[j] = 0;
+  for (int j = 0; j < 8; ++j) N[j] = 0;
 
-  int u, v;
-  bool act;
-  line_pixel(L, W, H, line, 0, u, v, act);
-  uint4 ca = make_uint4(0, 0, 0, 0), cb = ca;
-  if (act) {
-    const uint4* src = reinterpret_cast<const uint4*>(cost + ((size_t)v * W + u) * D + 32 * g);
-    ca = __ldg(src);
-    cb = __ldg(src + 1);
+  uint4 ring[kPrefetch];
+#pragma unroll
+  for (int k = 0; k < kPrefetch; ++k) {
+    int u, v;
+    bool act;
+    line_pixel(L, W, H, line, k, u, v, act);
+    ring[k] = make_uint4(0, 0, 0, 0);
+    if (act && k < L.nsteps) ring[k] = __ldg(reinterpret_cast<const uint4*>(csrc + ((size_t)v * W + u) * D));
   }
-  for (int s = 0; s < L.nsteps; ++s) {
-    int un, vn;
-    bool actn;
-    line_pixel(L, W, H, line, s + 1, un, vn, actn);
-    actn = actn && s + 1 < L.nsteps;
-    uint4 na = make_uint4(0, 0, 0, 0), nb = na;
-    if (actn) {
-      const uint4* src = reinterpret_cast<const uint4*>(cost + ((size_t)vn * W + un) * D + 32 * g);
-      na = __ldg(src);
-      nb = __ldg(src + 1);
+  for (int s0 = 0; s0 < L.nsteps; s0 += kPrefetch) {
+#pragma unroll
+    for (int k = 0; k < kPrefetch; ++k) {
+      const int s = s0 + k;
+      if (s >= L.nsteps) break;  // warp-uniform
+      int u, v;
+      bool act;
+      line_pixel(L, W, H, line, s, u, v, act);
+      const uint32_t raw[4] = {ring[k].x, ring[k].y, ring[k].z, ring[k].w};
+      {  // refill this slot with the cost of step s + kPrefetch
+        int un, vn;
+        bool an;
+        line_pixel(L, W, H, line, s + kPrefetch, un, vn, an);
+        if (an && s + kPrefetch < L.nsteps)
+          ring[k] = __ldg(reinterpret_cast<const uint4*>(csrc + ((size_t)vn * W + un) * D));
+      }
+      // neighbours across the lane boundaries of this line's lane group
+      uint32_t prevHi = kBig2, nextLo = kBig2;
+      if constexpr (G > 1) {
+        uint32_t up = __shfl_up_sync(kFull, N[7], 1, G);
+        uint32_t dn = __shfl_down_sync(kFull, N[0], 1, G);
+        if (g > 0) prevHi = up;
+        if (g < G - 1) nextLo = dn;
+      }
+      const uint32_t left0 = __byte_perm(prevHi, N[7], 0x5432);
+      const uint32_t right7 = __byte_perm(N[0], nextLo, 0x5432);
+      uint32_t Lw[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        uint32_t lft = j == 0 ? left0 : N[j - 1];
+        uint32_t rgt = j == 7 ? right7 : N[j + 1];
+        uint32_t t = __vimin3_u16x2(lft, rgt, K21x2);
+        t = __viaddmin_u16x2(t, P1x2, N[j]);
+        uint32_t c = __byte_perm(raw[j >> 1], 0, (j & 1) ? 0x4342 : 0x4140);
+        Lw[j] = __vadd2(t, c);
+      }
+      uint32_t m = __vminu2(__vminu2(__vminu2(Lw[0], Lw[1]), __vminu2(Lw[2], Lw[3])),
+                            __vminu2(__vminu2(Lw[4], Lw[5]), __vminu2(Lw[6], Lw[7])));
+      m = __vminu2(m, __byte_perm(m, m, 0x1032));  // both halves = min of the two halves
+#pragma unroll
+      for (int o = 1; o < G; o <<= 1) m = __vminu2(m, __shfl_xor_sync(kFull, m, o, G));
+      if (act) {
+        uint4 w;
+        w.x = __byte_perm(Lw[0], Lw[1], 0x6420);
+        w.y = __byte_perm(Lw[2], Lw[3], 0x6420);
+        w.z = __byte_perm(Lw[4], Lw[5], 0x6420);
+        w.w = __byte_perm(Lw[6], Lw[7], 0x6420);
+        __stcs(reinterpret_cast<uint4*>(dst_vol + ((size_t)v * W + u) * D + 16 * g), w);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) N[j] = __vsub2(Lw[j], m);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) N[j] = 0;
+      }
     }
-    const uint32_t raw[8] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
-    // neighbours across the lane boundaries of this line's lane group
-    uint32_t prevHi = kBig2, nextLo = kBig2;
-    if constexpr (G > 1) {
-      uint32_t up = __shfl_up_sync(kFull, N[15], 1, G);
-      uint32_t dn = __shfl_down_sync(kFull, N[0], 1, G);
-      if (g > 0) prevHi = up;
-      if (g < G - 1) nextLo = dn;
-    }
-    const uint32_t left0 = __byte_perm(prevHi, N[15], 0x5432);
-    const uint32_t right15 = __byte_perm(N[0], nextLo, 0x5432);
-    uint32_t Lw[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      uint32_t lft = j == 0 ? left0 : N[j - 1];
-      uint32_t rgt = j == 15 ? right15 : N[j + 1];
-      uint32_t t = __vimin3_u16x2(lft, rgt, K21x2);
-      t = __viaddmin_u16x2(t, P1x2, N[j]);
-      uint32_t c = __byte_perm(raw[j >> 1], 0, (j & 1) ? 0x4342 : 0x4140);
-      Lw[j] = __vadd2(t, c);
-    }
-    uint32_t m8[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) m8[j] = __vminu2(Lw[2 * j], Lw[2 * j + 1]);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) m8[j] = __vminu2(m8[j], m8[j + 4]);
-    uint32_t m = __vminu2(__vminu2(m8[0], m8[1]), __vminu2(m8[2], m8[3]));
-    m = __vminu2(m, __byte_perm(m, m, 0x1032));  // both halves = min of the two halves
-#pragma unroll
-    for (int o = 1; o < G; o <<= 1) m = __vminu2(m, __shfl_xor_sync(kFull, m, o, G));
-    if (act) {
-      uint32_t w[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) w[i] = __byte_perm(Lw[2 * i], Lw[2 * i + 1], 0x6420);
-      uint4* dst = reinterpret_cast<uint4*>(dst_vol + ((size_t)v * W + u) * D + 32 * g);
-      __stcs(dst, make_uint4(w[0], w[1], w[2], w[3]));
-      __stcs(dst + 1, make_uint4(w[4], w[5], w[6], w[7]));
-#pragma unroll
-      for (int j = 0; j < 16; ++j) N[j] = __vsub2(Lw[j], m);
-    } else {
-#pragma unroll
-      for (int j = 0; j < 16; ++j) N[j] = 0;
-    }
-    ca = na;
-    cb = nb;
-    u = un;
-    v = vn;
-    act = actn;
   }
 }
 
 // ------------------------------------------------------------- volume sums and Eq. (9)
 constexpr int kWtaThreads = 128;
 
-// Loads this thread's 32 disparities of S as planar u16x2 pairs (d = 32g + j, 32g + 16 + j).
+// Loads this thread's 16 disparities of S as planar u16x2 pairs (d = 16g + j, 16g + 8 + j).
 __device__ __forceinline__ void load_S_il(const uint8_t* __restrict__ vols, int ndirs,
-                                          size_t vol_bytes, size_t off, uint32_t sw[16]) {
+                                          size_t vol_bytes, size_t off, uint32_t sw[8]) {
 #pragma unroll
-  for (int j = 0; j < 16; ++j) sw[j] = 0;
+  for (int j = 0; j < 8; ++j) sw[j] = 0;
   for (int r = 0; r < ndirs; ++r) {
-    const uint4* src = reinterpret_cast<const uint4*>(vols + (size_t)r * vol_bytes + off);
-    uint4 a = __ldcs(src), b = __ldcs(src + 1);
-    const uint32_t raw[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    uint4 a = __ldcs(reinterpret_cast<const uint4*>(vols + (size_t)r * vol_bytes + off));
+    const uint32_t raw[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-    for (int j = 0; j < 16; ++j)
+    for (int j = 0; j < 8; ++j)
       sw[j] = __vadd2(sw[j], __byte_perm(raw[j >> 1], 0, (j & 1) ? 0x4342 : 0x4140));
   }
 }
 
 __device__ __forceinline__ void load_S_nat(const uint16_t* __restrict__ S, size_t off,
-                                           uint32_t sw[16]) {
+                                           uint32_t sw[8]) {
   const uint4* src = reinterpret_cast<const uint4*>(S + off);
-  uint32_t n[16];
+  uint4 q0 = __ldg(src), q1 = __ldg(src + 1);
+  const uint32_t n[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};  // n[k]: d = 2k, 2k+1
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    uint4 q = __ldg(src + i);
-    n[4 * i] = q.x;
-    n[4 * i + 1] = q.y;
-    n[4 * i + 2] = q.z;
-    n[4 * i + 3] = q.w;
+  for (int j = 0; j < 8; ++j)
+    sw[j] = __byte_perm(n[j >> 1], n[4 + (j >> 1)], (j & 1) ? 0x7632 : 0x5410);
+}
+
+// Natural-order u32 words k = 0..7 (d = 2k, 2k + 1) from planar pairs.
+__device__ __forceinline__ void planar_to_natural(const uint32_t sw[8], uint32_t o[8]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    o[k] = __byte_perm(sw[2 * k], sw[2 * k + 1], 0x5410);
+    o[4 + k] = __byte_perm(sw[2 * k], sw[2 * k + 1], 0x7632);
   }
-  // n[k] holds d = 2k, 2k+1 (relative to the group)
-#pragma unroll
-  for (int j = 0; j < 16; ++j)
-    sw[j] = __byte_perm(n[j >> 1], n[8 + (j >> 1)], (j & 1) ? 0x7632 : 0x5410);
 }
 
 __global__ void __launch_bounds__(kWtaThreads) k_sum_volumes(const uint8_t* __restrict__ vols,
@@ -367,20 +358,15 @@ __global__ void __launch_bounds__(kWtaThreads) k_sum_volumes(const uint8_t* __re
                                                              uint16_t* __restrict__ S) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_groups) return;
-  uint32_t sw[16];
-  load_S_il(vols, ndirs, vol_bytes, 32 * t, sw);
-  uint32_t o[16];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    o[k] = __byte_perm(sw[2 * k], sw[2 * k + 1], 0x5410);
-    o[8 + k] = __byte_perm(sw[2 * k], sw[2 * k + 1], 0x7632);
-  }
-  uint4* d = reinterpret_cast<uint4*>(S + 32 * t);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) d[i] = make_uint4(o[4 * i], o[4 * i + 1], o[4 * i + 2], o[4 * i + 3]);
+  uint32_t sw[8], o[8];
+  load_S_il(vols, ndirs, vol_bytes, 16 * t, sw);
+  planar_to_natural(sw, o);
+  uint4* d = reinterpret_cast<uint4*>(S + 16 * t);
+  d[0] = make_uint4(o[0], o[1], o[2], o[3]);
+  d[1] = make_uint4(o[4], o[5], o[6], o[7]);
 }
 
-// One block covers P = 128 / G pixels of one row; G = D / 32 threads per pixel.
+// One block covers P = 128 / G pixels of one row; G = D / 16 threads per pixel.
 // Writes d* (int16) and the sub-pixel value, and folds the right-view candidates of its pixels
 // into rkeys[v][x] = min over d of (S(x + d, d) << 8 | d) with one atomicMin per covered x.
 __global__ void __launch_bounds__(kWtaThreads) k_wta(const uint8_t* __restrict__ vols, int ndirs,
@@ -390,7 +376,7 @@ __global__ void __launch_bounds__(kWtaThreads) k_wta(const uint8_t* __restrict__
                                                      float* __restrict__ dsub,
                                                      uint32_t* __restrict__ rkeys) {
   extern __shared__ uint16_t sS[];  // [P][D]
-  const int G = D >> 5;
+  const int G = D >> 4;
   const int P = kWtaThreads / G;
   const int v = blockIdx.y;
   const int u0 = blockIdx.x * P;
@@ -399,22 +385,20 @@ __global__ void __launch_bounds__(kWtaThreads) k_wta(const uint8_t* __restrict__
   const int u = u0 + pix;
   uint32_t key = 0xffffffffu;
   if (pix < Peff) {
-    size_t off = ((size_t)v * W + u) * D + 32 * g;
-    uint32_t sw[16];
+    size_t off = ((size_t)v * W + u) * D + 16 * g;
+    uint32_t sw[8], o[8];
     if (S)
       load_S_nat(S, off, sw);
     else
       load_S_il(vols, ndirs, vol_bytes, off, sw);
-    uint16_t* row = sS + pix * D + 32 * g;
+    planar_to_natural(sw, o);
+    uint4* row = reinterpret_cast<uint4*>(sS + pix * D + 16 * g);
+    row[0] = make_uint4(o[0], o[1], o[2], o[3]);
+    row[1] = make_uint4(o[4], o[5], o[6], o[7]);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      reinterpret_cast<uint32_t*>(row)[k] = __byte_perm(sw[2 * k], sw[2 * k + 1], 0x5410);
-      reinterpret_cast<uint32_t*>(row + 16)[k] = __byte_perm(sw[2 * k], sw[2 * k + 1], 0x7632);
-    }
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      uint32_t klo = ((sw[j] & 0xffffu) << 8) | (uint32_t)(32 * g + j);
-      uint32_t khi = ((sw[j] >> 16) << 8) | (uint32_t)(32 * g + 16 + j);
+    for (int j = 0; j < 8; ++j) {
+      uint32_t klo = ((sw[j] & 0xffffu) << 8) | (uint32_t)(16 * g + j);
+      uint32_t khi = ((sw[j] >> 16) << 8) | (uint32_t)(16 * g + 8 + j);
       key = min(key, min(klo, khi));
     }
   }
@@ -508,7 +492,7 @@ void launch_census(cudaStream_t s, const uint8_t* img, int W, int H, size_t pitc
 void launch_cost(cudaStream_t s, const uint32_t* cl, const uint32_t* cr, int W, int H, int D,
                  int layout, uint8_t* cost) {
   if (layout == 1) {
-    int P = kCostThreads / (D / 32);
+    int P = kCostThreads / (D / 16);
     dim3 grid((W + P - 1) / P, H);
     k_cost_il<<<grid, kCostThreads, 0, s>>>(cl, cr, W, D, cost);
   } else {
@@ -520,18 +504,18 @@ void launch_cost(cudaStream_t s, const uint32_t* cl, const uint32_t* cr, int W, 
 
 void launch_to_interleaved(cudaStream_t s, const uint8_t* natural, size_t n_pix, int D,
                            uint8_t* out) {
-  size_t n = n_pix * (size_t)(D / 32);
+  size_t n = n_pix * (size_t)(D / 16);
   k_to_interleaved<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(natural, n, out);
 }
 
 void launch_to_natural(cudaStream_t s, const uint8_t* inter, size_t n_pix, int D, uint8_t* out) {
-  size_t n = n_pix * (size_t)(D / 32);
+  size_t n = n_pix * (size_t)(D / 16);
   k_to_natural<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(inter, n, out);
 }
 
 void launch_aggregate(cudaStream_t s, const uint8_t* cost_il, int W, int H, int D,
                       const DirSet& dirs, int P1, int P2, uint8_t* out, size_t vol_bytes) {
-  int G = D / 32;
+  int G = D / 16;
   int maxlines = 0;
   for (int r = 0; r < dirs.n; ++r) {
     int n = dirs.dy[r] == 0 ? H : (dirs.dx[r] == 0 ? W : W + H - 1);
@@ -542,17 +526,17 @@ void launch_aggregate(cudaStream_t s, const uint8_t* cost_il, int W, int H, int 
   uint32_t P1x2 = (uint32_t)P1 * 0x10001u;
   uint32_t K21x2 = (uint32_t)(P2 - P1) * 0x10001u;
   switch (G) {
-    case 1: k_aggregate<1><<<grid, kAggWarps * 32, 0, s>>>(cost_il, out, W, H, D, dirs, P1x2, K21x2, vol_bytes); break;
     case 2: k_aggregate<2><<<grid, kAggWarps * 32, 0, s>>>(cost_il, out, W, H, D, dirs, P1x2, K21x2, vol_bytes); break;
     case 4: k_aggregate<4><<<grid, kAggWarps * 32, 0, s>>>(cost_il, out, W, H, D, dirs, P1x2, K21x2, vol_bytes); break;
     case 8: k_aggregate<8><<<grid, kAggWarps * 32, 0, s>>>(cost_il, out, W, H, D, dirs, P1x2, K21x2, vol_bytes); break;
+    case 16: k_aggregate<16><<<grid, kAggWarps * 32, 0, s>>>(cost_il, out, W, H, D, dirs, P1x2, K21x2, vol_bytes); break;
     default: break;  // the API admits D in {32, 64, 128, 256} only
   }
 }
 
 void launch_sum_volumes(cudaStream_t s, const uint8_t* vols, int ndirs, size_t vol_bytes, int W,
                         int H, int D, uint16_t* S) {
-  size_t n = (size_t)W * H * (D / 32);
+  size_t n = (size_t)W * H * (D / 16);
   k_sum_volumes<<<(unsigned)((n + kWtaThreads - 1) / kWtaThreads), kWtaThreads, 0, s>>>(
       vols, ndirs, vol_bytes, n, S);
 }
@@ -560,7 +544,7 @@ void launch_sum_volumes(cudaStream_t s, const uint8_t* vols, int ndirs, size_t v
 void launch_wta(cudaStream_t s, const uint8_t* vols, int ndirs, size_t vol_bytes,
                 const uint16_t* S, int W, int H, int D, int16_t* d_int, float* dsub,
                 uint32_t* rkeys) {
-  int G = D / 32;
+  int G = D / 16;
   int P = kWtaThreads / G;
   dim3 grid((W + P - 1) / P, H);
   size_t smem = (size_t)P * D * sizeof(uint16_t);
