@@ -185,95 +185,104 @@ __global__ void k_to_natural(const uint8_t* __restrict__ in, size_t n_groups,
 // ----------------------------------------------------------------------------- Eq. (8)
 constexpr int kAggWarps = 4;
 
-struct LineGeom {
-  int dx, dy, nlines, nsteps, vlo, vhi;
-};
-
-__device__ __forceinline__ void line_pixel(const LineGeom& L, int W, int H, int line, int s,
-                                           int& u, int& v, bool& act) {
-  if (L.dy == 0) {
-    v = line;
-    u = L.dx > 0 ? s : W - 1 - s;
-    act = line < L.nlines;
-  } else {
-    v = L.dy > 0 ? L.vlo + s : L.vhi - s;
-    u = L.dx == 0 ? line : (L.dx == L.dy ? line - (H - 1) + v : line - v);
-    act = line < L.nlines && u >= 0 && u < W;
-  }
-}
-
 constexpr int kPrefetch = 8;  // cost loads in flight per lane (steps ahead)
 
+// Every line of direction (dx, dy) is walked by a step index s; the pixel at step s moves by a
+// constant byte stride through the [H][W][D] volumes, and the line lies inside the image for one
+// contiguous range of s.  Horizontal lines are the rows (s runs along u); all other lines step
+// one row per s (s runs along v, in the direction of dy), and diagonal lines are indexed by
+// u - v (dx == dy) or u + v (dx == -dy).
+struct LineWalk {
+  long long off0;   // byte offset of step 0 (may lie outside the image)
+  long long delta;  // byte stride per step
+  int s_first, s_last, nsteps;
+};
+
+__device__ __forceinline__ LineWalk line_walk(int dx, int dy, int W, int H, int D, int line,
+                                              int first, int last, bool valid) {
+  LineWalk w;
+  if (dy == 0) {  // row `line`, s along u
+    const int u0 = dx > 0 ? 0 : W - 1;
+    w.off0 = ((long long)line * W + u0) * D;
+    w.delta = (long long)dx * D;
+    w.nsteps = W;
+    w.s_first = 0;
+    w.s_last = valid ? W - 1 : -1;
+    return w;
+  }
+  int vlo = 0, vhi = H - 1;
+  if (dx != 0) {  // the rows any line of this warp touches
+    if (dx == dy) {
+      vlo = max(0, H - 1 - last);
+      vhi = min(H - 1, W + H - 2 - first);
+    } else {
+      vlo = max(0, first - W + 1);
+      vhi = min(H - 1, last);
+    }
+  }
+  w.nsteps = vhi - vlo + 1;
+  const int v0 = dy > 0 ? vlo : vhi;
+  const int u0 = dx == 0 ? line : (dx == dy ? line - (H - 1) + v0 : line - v0);  // u at step 0
+  w.off0 = ((long long)v0 * W + u0) * D;
+  w.delta = ((long long)dy * W + dx) * D;
+  // steps with 0 <= u0 + s*dx <= W-1 and 0 <= s < nsteps
+  int lo = 0, hi = w.nsteps - 1;
+  if (dx > 0) {
+    lo = max(lo, -u0);
+    hi = min(hi, W - 1 - u0);
+  } else if (dx < 0) {
+    lo = max(lo, u0 - (W - 1));
+    hi = min(hi, u0);
+  }
+  w.s_first = lo;
+  w.s_last = valid ? hi : -1;
+  return w;
+}
+
 template <int G>
-__global__ void __launch_bounds__(kAggWarps * 32) k_aggregate(const uint8_t* __restrict__ cost,
-                                                              uint8_t* __restrict__ out, int W,
-                                                              int H, int D, DirSet dirs,
-                                                              uint32_t P1x2, uint32_t K21x2,
-                                                              size_t vol_bytes) {
+__global__ void __launch_bounds__(kAggWarps * 32, 5) k_aggregate(const uint8_t* __restrict__ cost,
+                                                                 uint8_t* __restrict__ out, int W,
+                                                                 int H, int D, DirSet dirs,
+                                                                 uint32_t P1x2, uint32_t K21x2,
+                                                                 size_t vol_bytes) {
   constexpr int LPW = 32 / G;  // lines per warp
   const int r = blockIdx.y;
-  LineGeom L;
-  L.dx = dirs.dx[r];
-  L.dy = dirs.dy[r];
-  if (L.dy == 0) {
-    L.nlines = H;
-    L.nsteps = W;
-  } else if (L.dx == 0) {
-    L.nlines = W;
-    L.nsteps = H;
-  } else {
-    L.nlines = W + H - 1;
-  }
+  const int dx = dirs.dx[r], dy = dirs.dy[r];
+  const int nlines = dy == 0 ? H : (dx == 0 ? W : W + H - 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane % G;
   const int first = (blockIdx.x * kAggWarps + warp) * LPW;
-  if (first >= L.nlines) return;  // the whole warp leaves together
+  if (first >= nlines) return;  // the whole warp leaves together
   const int line = first + lane / G;
-  const int last = min(first + LPW, L.nlines) - 1;
-  L.vlo = 0;
-  L.vhi = H - 1;
-  if (L.dy != 0 && L.dx != 0) {
-    if (L.dx == L.dy) {  // u - v constant
-      L.vlo = max(0, H - 1 - last);
-      L.vhi = min(H - 1, W + H - 2 - first);
-    } else {  // u + v constant
-      L.vlo = max(0, first - W + 1);
-      L.vhi = min(H - 1, last);
-    }
-    L.nsteps = L.vhi - L.vlo + 1;
-  }
-  uint8_t* dst_vol = out + (size_t)r * vol_bytes;
+  const int last = min(first + LPW, nlines) - 1;
+  const LineWalk lw = line_walk(dx, dy, W, H, D, line, first, last, line < nlines);
   const uint8_t* csrc = cost + 16 * g;
+  uint8_t* dst = out + (size_t)r * vol_bytes + 16 * g;
 
   uint32_t N[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) N[j] = 0;
 
   uint4 ring[kPrefetch];
+  long long pf_off = lw.off0;  // offset of the step being prefetched
 #pragma unroll
   for (int k = 0; k < kPrefetch; ++k) {
-    int u, v;
-    bool act;
-    line_pixel(L, W, H, line, k, u, v, act);
     ring[k] = make_uint4(0, 0, 0, 0);
-    if (act && k < L.nsteps) ring[k] = __ldg(reinterpret_cast<const uint4*>(csrc + ((size_t)v * W + u) * D));
+    if (k >= lw.s_first && k <= lw.s_last) ring[k] = __ldg(reinterpret_cast<const uint4*>(csrc + pf_off));
+    pf_off += lw.delta;
   }
-  for (int s0 = 0; s0 < L.nsteps; s0 += kPrefetch) {
+  long long st_off = lw.off0;  // offset of the current step
+  for (int s0 = 0; s0 < lw.nsteps; s0 += kPrefetch) {
 #pragma unroll
     for (int k = 0; k < kPrefetch; ++k) {
       const int s = s0 + k;
-      if (s >= L.nsteps) break;  // warp-uniform
-      int u, v;
-      bool act;
-      line_pixel(L, W, H, line, s, u, v, act);
+      if (s >= lw.nsteps) break;  // warp-uniform
+      const bool act = s >= lw.s_first && s <= lw.s_last;
       const uint32_t raw[4] = {ring[k].x, ring[k].y, ring[k].z, ring[k].w};
-      {  // refill this slot with the cost of step s + kPrefetch
-        int un, vn;
-        bool an;
-        line_pixel(L, W, H, line, s + kPrefetch, un, vn, an);
-        if (an && s + kPrefetch < L.nsteps)
-          ring[k] = __ldg(reinterpret_cast<const uint4*>(csrc + ((size_t)vn * W + un) * D));
-      }
+      const int sp = s + kPrefetch;
+      if (sp >= lw.s_first && sp <= lw.s_last)
+        ring[k] = __ldg(reinterpret_cast<const uint4*>(csrc + pf_off));
+      pf_off += lw.delta;
       // neighbours across the lane boundaries of this line's lane group
       uint32_t prevHi = kBig2, nextLo = kBig2;
       if constexpr (G > 1) {
@@ -305,13 +314,14 @@ __global__ void __launch_bounds__(kAggWarps * 32) k_aggregate(const uint8_t* __r
         w.y = __byte_perm(Lw[2], Lw[3], 0x6420);
         w.z = __byte_perm(Lw[4], Lw[5], 0x6420);
         w.w = __byte_perm(Lw[6], Lw[7], 0x6420);
-        __stcs(reinterpret_cast<uint4*>(dst_vol + ((size_t)v * W + u) * D + 16 * g), w);
+        __stcs(reinterpret_cast<uint4*>(dst + st_off), w);
 #pragma unroll
         for (int j = 0; j < 8; ++j) N[j] = __vsub2(Lw[j], m);
       } else {
 #pragma unroll
         for (int j = 0; j < 8; ++j) N[j] = 0;
       }
+      st_off += lw.delta;
     }
   }
 }
