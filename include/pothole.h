@@ -199,6 +199,26 @@ pd_status pd_moments(pd_ctx* ctx, const float* D1, int W, int H, int64_t* sums);
 pd_status pd_transform(pd_ctx* ctx, const float* D1, int W, int H, int order, float delta_dt,
                        pd_road_model* fitted, float* D2);
 
+/* Allocation-free form of pd_transform, with no counterpart in the paper.  It is for callers
+ * that may not allocate device memory: code running while a stream is captured into a CUDA graph
+ * (allocation is not capturable), real-time loops that cannot afford cudaMalloc / cudaFree (the
+ * latter synchronises the whole device), and processes whose device memory is owned by another
+ * allocator.  It needs no pd_ctx and calls no cudaMalloc, cudaFree or other allocating routine:
+ * its scratch is one fixed 512 KiB array in the library's device image, which every GPU that
+ * loads the library holds until the process exits.
+ *  - Same arguments and results as pd_transform, enqueued on `stream` (a cudaStream_t; NULL is
+ *    the legacy default stream) of the caller's current device.
+ *  - Limits: W, H <= 4096 and W * H <= 4194304 (4 Mpixel); larger images return
+ *    PD_ERR_INVALID_ARG without launching anything.  So do NULL D1/D2, an order other than 1 or 2
+ *    and a non-finite delta_dt.  Launch failures return PD_ERR_CUDA.
+ *  - The first call on a device looks up the array's device address on that device (the current
+ *    one); make that first call before any stream capture.
+ *  - All calls share the one array: calls that may overlap on the GPU (different streams, or
+ *    different host threads on one device) race and must be serialised by the caller.  Each call
+ *    overwrites what the previous one left there before reading it. */
+pd_status pd_transform_noalloc(const float* D1, int W, int H, int order, float delta_dt,
+                               pd_road_model* fitted, float* D2, void* stream);
+
 /* ---------------------------------------------------------------- Sec. II-D: superpixels */
 
 /* SLIC on D2: grid interval S = sqrt(W H / K), nx = round(W / S), ny = round(H / S) seeds moved

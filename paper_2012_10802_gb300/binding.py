@@ -89,6 +89,7 @@ SIGNATURES = {
     "pd_pothole_mask": [_P, _P, _P, _P, _i, _i, _f, _i, _P, _P, _P],
     "pd_run_pipeline": [_P, _P, _P, _i, _i, _z, C.POINTER(RoadModel), C.POINTER(Params),
                         C.POINTER(Outputs), C.POINTER(StageTimes)],
+    "pd_transform_noalloc": [_P, _i, _i, _i, _f, _P, _P, _P],
     "pd_profile_enable": [_P, _i],
     "pd_profile_read": [_P, C.POINTER(Profile)],
 }
@@ -325,3 +326,12 @@ def pd_profile_read(ctx):
     p = Profile()
     ctx.check(lib().pd_profile_read(ctx.h, C.byref(p)))
     return p.as_dict()
+
+
+def pd_transform_noalloc(D1, order, delta_dt, fitted, D2, stream=None):
+    """The allocation-free transform: no context, fixed library scratch; outputs must be given."""
+    H, W = D1.shape
+    if stream is None:
+        stream = torch.cuda.current_stream(D1.device)
+    return lib().pd_transform_noalloc(_ptr(D1), W, H, order, float(delta_dt), _ptr(fitted),
+                                      _ptr(D2), C.c_void_p(stream.cuda_stream))

@@ -1,7 +1,17 @@
 // Sec. II-C on the GPU: exact moment sums of the road disparities, the roll / road-model fit of
 // Eqs. (11)-(12) on the device (a grid of angles over many SMs, then one refining block; no host
 // round trip), and the Eq. (13) transformation.
+#include <math.h>
+
+#include <mutex>
+
 #include "common.cuh"
+
+// Fixed scratch of the allocation-free transform entry point (pd_transform_noalloc): every GPU
+// that loads the library holds it until the process exits.
+static constexpr size_t kNoAllocScratchBytes = 512 * 1024;
+static constexpr long long kNoAllocMaxPixels = 4194304;  // W * H limit that fits the scratch
+static __device__ __align__(256) unsigned char g_transform_scratch[kNoAllocScratchBytes];
 
 namespace pd {
 
@@ -382,3 +392,67 @@ void launch_d2(cudaStream_t s, const float* D1, int W, int H, const RoadCoefF* c
 }
 
 }  // namespace pd
+
+// ---------------------------------------------------------------- allocation-free transform
+
+namespace pd {
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+}  // namespace
+
+}  // namespace pd
+
+extern "C" pd_status pd_transform_noalloc(const float* D1, int W, int H, int order,
+                                          float delta_dt, pd_road_model* fitted, float* D2,
+                                          void* stream) {
+  using namespace pd;
+  if (!D1 || !D2) return PD_ERR_INVALID_ARG;
+  if (W < 1 || H < 1 || W > kMaxImage || H > kMaxImage) return PD_ERR_INVALID_ARG;
+  if ((long long)W * (long long)H > kNoAllocMaxPixels) return PD_ERR_INVALID_ARG;
+  if (order != 1 && order != 2) return PD_ERR_INVALID_ARG;
+  if (!isfinite(delta_dt)) return PD_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return PD_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return PD_ERR_UNSUPPORTED;
+  void* base = nullptr;
+  {
+    // one-time set-up per device, on the caller's current device: the device address of the
+    // fixed scratch (the array's name in host code is not a device address)
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_transform_scratch);
+      if (e != cudaSuccess || p == nullptr) {
+        cudaGetLastError();
+        return PD_ERR_CUDA;
+      }
+      g_noalloc_ptr[dev] = p;
+    }
+    base = g_noalloc_ptr[dev];
+  }
+  size_t need = 0;
+  carve_size<uint8_t>(need, moments_scratch_bytes(W, H));
+  carve_size<int64_t>(need, 46);
+  carve_size<pd_road_model>(need, 1);
+  carve_size<RoadCoefF>(need, 1);
+  carve_size<uint8_t>(need, roll_scratch_bytes());
+  if (need > kNoAllocScratchBytes) return PD_ERR_INVALID_ARG;
+  Carve c(base);
+  void* part = c.take<uint8_t>(moments_scratch_bytes(W, H));
+  int64_t* sums = c.take<int64_t>(46);
+  pd_road_model* fit = c.take<pd_road_model>(1);
+  RoadCoefF* coef = c.take<RoadCoefF>(1);
+  double* grid = reinterpret_cast<double*>(c.take<uint8_t>(roll_scratch_bytes()));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // every piece is fully written before it is read, so nothing needs clearing between calls
+  launch_moments(s, D1, W, H, part, sums);
+  launch_roll_solve(s, sums, order, W, H, fitted ? fitted : fit, coef, grid);
+  launch_d2(s, D1, W, H, coef, delta_dt, D2);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? PD_OK : PD_ERR_CUDA;
+}
