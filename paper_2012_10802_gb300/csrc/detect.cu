@@ -108,15 +108,23 @@ __global__ void __launch_bounds__(kTileThreads) k_slic_assign(
     // conservative box test (1 px margin); the exact test runs per pixel below
     const float bx0 = (float)x0 - 1.0f, bx1 = (float)(x0 + kTile), by0 = (float)y0 - 1.0f,
                 by1 = (float)(y0 + kTile);
-    for (int base = 0; base < n; base += kTileThreads) {
+    constexpr int kBatch = 8;  // centres per thread loaded together before the ordered scan
+    for (int base0 = 0; base0 < n; base0 += kBatch * kTileThreads) {
+      float bx[kBatch], byy[kBatch];
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b) {
+        int k = base0 + b * kTileThreads + tid;
+        bx[b] = k < n ? cx[k] : 0.f;
+        byy[b] = k < n ? cy[k] : 0.f;
+      }
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b) {
+      const int base = base0 + b * kTileThreads;
+      if (base >= n) break;  // block-uniform
       int k = base + tid;
       bool q = false;
-      float fx = 0.f, fy = 0.f;
-      if (k < n) {
-        fx = cx[k];
-        fy = cy[k];
-        q = (fx + Sf >= bx0) && (fx - Sf <= bx1) && (fy + Sf >= by0) && (fy - Sf <= by1);
-      }
+      float fx = bx[b], fy = byy[b];
+      if (k < n) q = (fx + Sf >= bx0) && (fx - Sf <= bx1) && (fy + Sf >= by0) && (fy - Sf <= by1);
       unsigned bal = __ballot_sync(0xffffffffu, q);
       if (lane == 0) wcount[warp] = __popc(bal);
       __syncthreads();
@@ -136,6 +144,7 @@ __global__ void __launch_bounds__(kTileThreads) k_slic_assign(
         ncand = tot;
       }
       __syncthreads();
+      }
     }
   }
   const int nc = ncand;
@@ -183,7 +192,7 @@ __global__ void __launch_bounds__(kTileThreads) k_slic_assign(
       }
       labels[p] = lab;
     }
-    q = __double2ll_rn((double)val * 1024.0);
+    q = __float2ll_rn(val * 1024.0f);  // exact scaling; rounds half to even like rint
   }
   // a label's slot is the same for every lane that has it, so grouping by label groups by slot;
   // lanes that kept an uncovered pixel's old label (slot -1) go straight to the global sums
@@ -287,7 +296,7 @@ __global__ void __launch_bounds__(256) k_thresh_hist(const float* __restrict__ D
         for (int dx = -1; dx <= 1; ++dx) {
           size_t q = (size_t)(v + dy) * W + (u + dx);
           if (!(D1[q] >= 0.0f)) ok = false;
-          long long qq = __double2ll_rn((double)D2[q] * 1024.0);
+          long long qq = __float2ll_rn(D2[q] * 1024.0f);
           if (dx == 0 && dy == 0)
             a = qq;
           else

@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(kMomThreads) k_moments_partial(const float* __
   for (size_t p = start + threadIdx.x; p < end; p += kMomThreads) {
     float d = D1[p];
     if (!(d >= 0.0f)) continue;
-    long long q = __double2ll_rn((double)d * 1024.0);
+    long long q = __float2ll_rn(d * 1024.0f);  // exact scaling; rounds half to even like rint
     int u = (int)(p % W), v = (int)(p / W);
     long long ut = 2LL * u - (W - 1), vt = 2LL * v - (H - 1);
     long long up[5], vp[5];
@@ -154,50 +154,82 @@ __device__ int spd_solve_d(int n, const double A[3][3], const double b[3], doubl
   return 0;
 }
 
-// Eq. (12) at one roll angle for a model of the given order; beta gets the Eq. (11) solution in
-// the basis 1, w_s, w_s^2 with w_s = (v~ cos(phi) - u~ sin(phi)) / sc.
-__device__ double e0min_d(const MomD& M, int order, double sc, double phi, double beta[3]) {
-  int n = order + 1;
-  double cs = cos(phi) / sc;
-  double ss = -sin(phi) / sc;
+// Eq. (12) for given cos(phi), sin(phi), by an LDL' factorisation of T'T (no square roots, three
+// divisions: FP64 runs at about one operation per clock per SM on this part, so the evaluation
+// is kept short).  E0min = d'd - sum_i y_i^2 / D_i with L y = T'd; beta = the Eq. (11) solution.
+__device__ double e0min_cs(const MomD& M, int order, double sc, double cphi, double sphi,
+                           double beta[3]) {
+  const int n = order + 1;
+  const double cs = cphi / sc, ss = -sphi / sc;
   double pc[5], ps[5];
   pc[0] = 1.0;
   ps[0] = 1.0;
+#pragma unroll
   for (int i = 1; i < 5; ++i) {
     pc[i] = pc[i - 1] * cs;
     ps[i] = ps[i - 1] * ss;
   }
-  double sw[5] = {0, 0, 0, 0, 0}, sqw[3] = {0, 0, 0};
-  for (int k = 0; k <= 2 * order; ++k) {
+  double sw[5] = {0, 0, 0, 0, 0}, b[3] = {0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    if (k > 2 * order) break;
     double acc = 0.0;
+#pragma unroll
     for (int j = 0; j <= k; ++j) acc += kBinomD[k][j] * pc[j] * ps[k - j] * M.m[k - j][j];
     sw[k] = acc;
   }
-  for (int k = 0; k <= order; ++k) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (k > order) break;
     double acc = 0.0;
+#pragma unroll
     for (int j = 0; j <= k; ++j) acc += kBinomD[k][j] * pc[j] * ps[k - j] * M.q[k - j][j];
-    sqw[k] = acc / 1024.0;
+    b[k] = acc / 1024.0;
   }
-  double A[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, b[3] = {0, 0, 0}, x[3] = {0, 0, 0};
-  for (int i = 0; i < n; ++i) {
-    b[i] = sqw[i];
-    for (int k = 0; k < n; ++k) A[i][k] = sw[i + k];
+  const double dd = M.qq / 1048576.0;
+  beta[0] = beta[1] = beta[2] = 0.0;
+  // A = [[sw0, sw1, sw2], [sw1, sw2, sw3], [sw2, sw3, sw4]] (top-left n x n block)
+  const double d0 = sw[0];
+  if (!(d0 > 0.0)) return INFINITY;
+  const double i0 = 1.0 / d0;
+  const double l10 = sw[1] * i0;
+  const double d1 = sw[2] - l10 * sw[1];
+  if (!(d1 > 0.0)) return INFINITY;
+  const double i1 = 1.0 / d1;
+  const double y0 = b[0], y1 = b[1] - l10 * y0;
+  if (n == 2) {
+    const double x1 = y1 * i1;
+    beta[1] = x1;
+    beta[0] = y0 * i0 - l10 * x1;
+    return dd - (y0 * y0 * i0 + y1 * y1 * i1);
   }
-  if (spd_solve_d(n, A, b, x) != 0) {
-    beta[0] = beta[1] = beta[2] = 0.0;
-    return INFINITY;
-  }
-  double dd = M.qq / 1048576.0;
-  double fit = 0.0;
-  for (int i = 0; i < n; ++i) fit += b[i] * x[i];
-  for (int i = 0; i < 3; ++i) beta[i] = i < n ? x[i] : 0.0;
-  return dd - fit;
+  const double l20 = sw[2] * i0;
+  const double l21 = (sw[3] - l20 * sw[1]) * i1;
+  const double d2 = sw[4] - l20 * sw[2] - l21 * l21 * d1;
+  if (!(d2 > 0.0)) return INFINITY;
+  const double i2 = 1.0 / d2;
+  const double y2 = b[2] - l20 * y0 - l21 * y1;
+  const double x2 = y2 * i2;
+  const double x1 = y1 * i1 - l21 * x2;
+  beta[2] = x2;
+  beta[1] = x1;
+  beta[0] = y0 * i0 - l10 * x1 - l20 * x2;
+  return dd - (y0 * y0 * i0 + y1 * y1 * i1 + y2 * y2 * i2);
 }
 
 constexpr int kGridN = 3001;
 constexpr double kGridStep = 1.7453292519943295e-04;  // 0.01 degree
-constexpr int kGridThreads = 128;
-constexpr int kRefineThreads = 128;
+constexpr int kRollWarp = 32;
+constexpr int kGridBlocks = (kGridN + kRollWarp - 1) / kRollWarp;
+constexpr int kRoundBlocks = 152;
+constexpr int kRoundPoints = kRoundBlocks * kRollWarp;  // shrinks the bracket ~2400x per round
+constexpr int kRefineRounds = 2;                        // 0.02 degree -> below 1e-10 rad
+
+struct RollBest {
+  double e;
+  int k;
+  int pad;
+};
 
 __device__ void load_moments(const int64_t* __restrict__ sums, MomD& M) {
   int k = 1;  // skip the count; m[0][0] is the same number
@@ -217,103 +249,139 @@ __device__ double coord_scale_d(int W, int H) {
   return sc;
 }
 
-// E0min on the 0.01-degree grid over +-15 degrees, one angle per thread across many SMs.
-__global__ void __launch_bounds__(kGridThreads) k_roll_grid(const int64_t* __restrict__ sums,
-                                                            int order, int W, int H,
-                                                            double* __restrict__ E) {
+__device__ __forceinline__ bool better(double e, int k, double eo, int ko) {
+  return eo < e || (eo == e && ko < k);
+}
+
+// Warp-wide (e, k) minimum, smallest k on ties; every lane gets the result.
+__device__ void warp_argmin(double& e, int& k) {
+  for (int o = 16; o > 0; o >>= 1) {
+    double eo = __shfl_xor_sync(0xffffffffu, e, o);
+    int ko = __shfl_xor_sync(0xffffffffu, k, o);
+    if (better(e, k, eo, ko)) {
+      e = eo;
+      k = ko;
+    }
+  }
+}
+
+// Minimum over n per-block results, by one warp.
+__device__ void reduce_best(const RollBest* __restrict__ res, int n, double& e, int& k) {
+  e = INFINITY;
+  k = 0x7fffffff;
+  for (int i = threadIdx.x & 31; i < n; i += 32)
+    if (better(e, k, res[i].e, res[i].k)) {
+      e = res[i].e;
+      k = res[i].k;
+    }
+  warp_argmin(e, k);
+}
+
+// Bracket [a, b] searched by refinement round `round` (1..kRefineRounds), or the final bracket
+// and winning angle after the last round: the best grid angle's neighbours, then for each round
+// the neighbours of its best interior point.
+__device__ void bracket_chain(const RollBest* __restrict__ res, int round, double& a, double& b,
+                              double& phi) {
+  double e;
+  int w;
+  reduce_best(res, kGridBlocks, e, w);
+  int best = w < kGridN ? w : 0;
+  int klo = best > 0 ? best - 1 : 0;
+  int khi = best < kGridN - 1 ? best + 1 : kGridN - 1;
+  a = (double)(klo - kGridN / 2) * kGridStep;
+  b = (double)(khi - kGridN / 2) * kGridStep;
+  phi = (double)(best - kGridN / 2) * kGridStep;
+  for (int q = 1; q < round; ++q) {
+    reduce_best(res + kGridBlocks + (q - 1) * kRoundBlocks, kRoundBlocks, e, w);
+    if (w >= kRoundPoints) w = kRoundPoints / 2;
+    const double h = (b - a) / (double)(kRoundPoints + 1);
+    phi = a + h * (double)(w + 1);
+    const double na = a + h * (double)w;
+    const double nb = a + h * (double)(w + 2);
+    a = na;
+    b = nb;
+  }
+}
+
+// Grid stage: E0min at the 0.01-degree angles over +-15 degrees, one angle per thread, one warp
+// per block so the FP64 work spreads over many SMs; each block writes its best (E, index).
+__global__ void __launch_bounds__(kRollWarp) k_roll_grid(const int64_t* __restrict__ sums,
+                                                         int order, int W, int H,
+                                                         RollBest* __restrict__ res) {
   __shared__ MomD M;
   if (threadIdx.x == 0) load_moments(sums, M);
   __syncthreads();
-  int k = blockIdx.x * kGridThreads + threadIdx.x;
-  if (k >= kGridN) return;
-  double beta[3];
-  E[k] = e0min_d(M, order, coord_scale_d(W, H), (double)(k - kGridN / 2) * kGridStep, beta);
-}
-
-// Block argmin of (value, index), smallest index on ties.  Returns the winner to every thread.
-__device__ void block_argmin(double e, int k, double* sE, int* sK, double& be, int& bk) {
-  sE[threadIdx.x] = e;
-  sK[threadIdx.x] = k;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) {
-      double eo = sE[threadIdx.x + s];
-      int ko = sK[threadIdx.x + s];
-      if (eo < sE[threadIdx.x] || (eo == sE[threadIdx.x] && ko < sK[threadIdx.x])) {
-        sE[threadIdx.x] = eo;
-        sK[threadIdx.x] = ko;
-      }
-    }
-    __syncthreads();
+  int k = blockIdx.x * kRollWarp + threadIdx.x;
+  double e = INFINITY, beta[3];
+  if (k < kGridN) {
+    double sp, cp;
+    sincos((double)(k - kGridN / 2) * kGridStep, &sp, &cp);
+    e = e0min_cs(M, order, coord_scale_d(W, H), cp, sp, beta);
   }
-  be = sE[0];
-  bk = sK[0];
-  __syncthreads();
+  int kk = k < kGridN ? k : 0x7fffffff;
+  warp_argmin(e, kk);
+  if (threadIdx.x == 0) res[blockIdx.x] = RollBest{e, kk, 0};
 }
 
-// Refines the roll (order 2: around the best grid angle, by rounds of kRefineThreads angles that
-// shrink the bracket about 64x each, to below 1e-12 rad; order 1: the least-squares plane in
-// closed form), solves Eq. (11) for the coefficients and writes the model and its float form.
-__global__ void __launch_bounds__(kRefineThreads) k_roll_refine(const int64_t* __restrict__ sums,
-                                                                const double* __restrict__ E,
-                                                                int order, int W, int H,
-                                                                pd_road_model* fitted,
-                                                                RoadCoefF* coef) {
+// Refinement round: kRoundPoints interior points of the current bracket.
+__global__ void __launch_bounds__(kRollWarp) k_roll_round(const int64_t* __restrict__ sums,
+                                                          int order, int W, int H, int round,
+                                                          RollBest* __restrict__ res) {
   __shared__ MomD M;
-  __shared__ double sE[kRefineThreads];
-  __shared__ int sK[kRefineThreads];
-  __shared__ double sPhi;
+  if (threadIdx.x == 0) load_moments(sums, M);
+  __syncthreads();
+  __shared__ double sa, ca;
+  double a, b, phi;
+  bracket_chain(res, round, a, b, phi);
+  if (threadIdx.x == 0) sincos(a, &sa, &ca);
+  __syncwarp();
+  const double h = (b - a) / (double)(kRoundPoints + 1);
+  const int i = blockIdx.x * kRollWarp + threadIdx.x;
+  // cos / sin of a + t by angle addition; |t| < 4e-4 rad, so the Taylor series below are exact to
+  // far below double rounding
+  const double t = h * (double)(i + 1), t2 = t * t;
+  const double ct = 1.0 - t2 * (0.5 - t2 * (1.0 / 24.0 - t2 * (1.0 / 720.0)));
+  const double st = t * (1.0 - t2 * (1.0 / 6.0 - t2 * (1.0 / 120.0 - t2 * (1.0 / 5040.0))));
+  double beta[3];
+  double e = e0min_cs(M, order, coord_scale_d(W, H), ca * ct - sa * st, sa * ct + ca * st, beta);
+  int k = i;
+  warp_argmin(e, k);
+  if (threadIdx.x == 0) res[kGridBlocks + (round - 1) * kRoundBlocks + blockIdx.x] = RollBest{e, k, 0};
+}
+
+// Final stage (one warp): the roll (order 2: the winner of the last round; order 1: the
+// least-squares plane in closed form), Eq. (11) for the coefficients, the model and its float
+// form for the transform kernel.
+__global__ void __launch_bounds__(kRollWarp) k_roll_final(const int64_t* __restrict__ sums,
+                                                          const RollBest* __restrict__ res,
+                                                          int order, int W, int H,
+                                                          pd_road_model* fitted,
+                                                          RoadCoefF* coef) {
+  __shared__ MomD M;
   if (threadIdx.x == 0) load_moments(sums, M);
   __syncthreads();
   const double sc = coord_scale_d(W, H);
-  double beta[3];
-  if (order == 1) {
-    if (threadIdx.x == 0) {
-      double phi = 0.0;
-      double s1 = sc, s2 = sc * sc;
-      double A[3][3] = {{M.m[0][0], M.m[0][1] / s1, M.m[1][0] / s1},
-                        {M.m[0][1] / s1, M.m[0][2] / s2, M.m[1][1] / s2},
-                        {M.m[1][0] / s1, M.m[1][1] / s2, M.m[2][0] / s2}};
-      double b[3] = {M.q[0][0] / 1024.0, M.q[0][1] / s1 / 1024.0, M.q[1][0] / s1 / 1024.0};
-      double x[3] = {0, 0, 0};
-      if (spd_solve_d(3, A, b, x) == 0 && x[1] != 0.0) phi = atan(-x[2] / x[1]);
-      sPhi = phi;
-    }
-  } else {
-    double be = INFINITY;
-    int bk = kGridN;
-    for (int k = threadIdx.x; k < kGridN; k += kRefineThreads) {
-      double e = E[k];
-      if (e < be) {
-        be = e;
-        bk = k;
-      }
-    }
-    block_argmin(be, bk, sE, sK, be, bk);
-    int best = bk < kGridN ? bk : 0;
-    int klo = best > 0 ? best - 1 : 0;
-    int khi = best < kGridN - 1 ? best + 1 : kGridN - 1;
-    double a = (double)(klo - kGridN / 2) * kGridStep;
-    double b = (double)(khi - kGridN / 2) * kGridStep;
-    double phi = 0.5 * (a + b);
-    for (int round = 0; round < 12 && (b - a) > 1e-12; ++round) {
-      const double h = (b - a) / (double)(kRefineThreads + 1);
-      double x = a + h * (double)(threadIdx.x + 1);
-      double e = e0min_d(M, order, sc, x, beta);
-      int t;
-      block_argmin(e, threadIdx.x, sE, sK, e, t);
-      phi = a + h * (double)(t + 1);
-      double na = a + h * (double)t;
-      double nb = a + h * (double)(t + 2);
-      a = na;
-      b = nb;
-    }
-    if (threadIdx.x == 0) sPhi = phi;
+  double phi = 0.0;
+  if (order == 2) {
+    double a, b;
+    bracket_chain(res, kRefineRounds + 1, a, b, phi);
   }
-  __syncthreads();
   if (threadIdx.x != 0) return;
-  const double phi = sPhi;
-  e0min_d(M, order, sc, phi, beta);
+  if (order == 1) {
+    double s1 = sc, s2 = sc * sc;
+    double A[3][3] = {{M.m[0][0], M.m[0][1] / s1, M.m[1][0] / s1},
+                      {M.m[0][1] / s1, M.m[0][2] / s2, M.m[1][1] / s2},
+                      {M.m[1][0] / s1, M.m[1][1] / s2, M.m[2][0] / s2}};
+    double b[3] = {M.q[0][0] / 1024.0, M.q[0][1] / s1 / 1024.0, M.q[1][0] / s1 / 1024.0};
+    double x[3] = {0, 0, 0};
+    if (spd_solve_d(3, A, b, x) == 0 && x[1] != 0.0) phi = atan(-x[2] / x[1]);
+  }
+  double beta[3];
+  {
+    double sp, cp;
+    sincos(phi, &sp, &cp);
+    e0min_cs(M, order, sc, cp, sp, beta);
+  }
   double k = 2.0 / sc;
   double vc = (double)(H - 1) * 0.5;
   double b0 = beta[0], b1 = beta[1], b2 = order == 2 ? beta[2] : 0.0;
@@ -364,7 +432,9 @@ size_t moments_scratch_bytes(int W, int H) {
   return n * kNumSums * sizeof(long long);
 }
 
-size_t roll_scratch_bytes() { return kGridN * sizeof(double); }
+size_t roll_scratch_bytes() {
+  return (size_t)(kGridBlocks + kRefineRounds * kRoundBlocks) * sizeof(RollBest);
+}
 
 void launch_moments(cudaStream_t s, const float* D1, int W, int H, void* scratch, int64_t* sums) {
   int nblocks = (int)(((size_t)W * H + kMomPixPerBlock - 1) / kMomPixPerBlock);
@@ -375,13 +445,15 @@ void launch_moments(cudaStream_t s, const float* D1, int W, int H, void* scratch
 
 int launch_roll_solve(cudaStream_t s, const int64_t* sums, int order, int W, int H,
                       pd_road_model* fitted, RoadCoefF* coef, double* grid_scratch) {
+  RollBest* res = reinterpret_cast<RollBest*>(grid_scratch);
   int n = 1;
   if (order == 2) {
-    k_roll_grid<<<(kGridN + kGridThreads - 1) / kGridThreads, kGridThreads, 0, s>>>(
-        sums, order, W, H, grid_scratch);
-    ++n;
+    k_roll_grid<<<kGridBlocks, kRollWarp, 0, s>>>(sums, order, W, H, res);
+    for (int r = 1; r <= kRefineRounds; ++r)
+      k_roll_round<<<kRoundBlocks, kRollWarp, 0, s>>>(sums, order, W, H, r, res);
+    n += 1 + kRefineRounds;
   }
-  k_roll_refine<<<1, kRefineThreads, 0, s>>>(sums, grid_scratch, order, W, H, fitted, coef);
+  k_roll_final<<<1, kRollWarp, 0, s>>>(sums, res, order, W, H, fitted, coef);
   return n;
 }
 

@@ -5,10 +5,11 @@
 // A line is owned by G = D/16 lanes of a warp; each lane keeps 16 disparities as 8 packed u16x2
 // words, word j holding (d = 16g + j, d = 16g + 8 + j).  With that pairing the d-1 / d+1
 // neighbours of word j are words j-1 / j+1, so the recurrence needs no byte shuffling: per word it
-// is one 3-input min, one fused add-min and one add (Hopper/Blackwell DPX instructions), and only
-// the two ends of a lane's range cross lanes.  The matching cost is computed once per (p, d) into
+// is one 3-input min and one fused add-min (Hopper/Blackwell DPX instructions) and one three-input
+// add that adds the cost and subtracts the previous minimum, and only the two ends of a lane's
+// range cross lanes.  The matching cost is computed once per (p, d) into
 // a uint8 volume (popcount is a quarter-rate instruction) and every direction reads it with one
-// 16-byte load per lane and step, issued kPrefetch steps ahead from a register ring.
+// 16-byte asynchronous copy per lane and step into a shared-memory ring, kStages - 1 steps ahead.
 #include <cstdio>
 
 #include "common.cuh"
@@ -23,8 +24,21 @@ constexpr uint32_t kBig2 = 0x3fff3fffu;  // "no neighbour": never the minimum, n
 __device__ __forceinline__ int clampi(int x, int lo, int hi) { return x < lo ? lo : (x > hi ? hi : x); }
 
 // ----------------------------------------------------------------------------- Eq. (6)
-// One warp per row: brute-force minimum of f(x, v) - delta_pt over x, evaluated in double in the
-// fixed operation order of the model definition (the library is built without FMA contraction).
+// One warp per row: minimum of f(x, v) - delta_pt over x = 0..W-1, each f evaluated in double in
+// the fixed operation order of the model definition (the library is built without FMA
+// contraction).  f is monotone in x for the linear model and convex or concave in x for the
+// quadratic one, so the minimum over all x lies at an end point or, for a convex quadratic, next
+// to the vertex: the warp evaluates both end points and the 64 columns around the vertex.
+__device__ __forceinline__ double road_minus(double t1, double uc, double vc, double sn, int order,
+                                             double a0, double a1, double a2, double delta_pt,
+                                             int x) {
+  double t2 = ((double)x - uc) * sn;
+  double vp = (t1 - t2) + vc;
+  double f = a0 + a1 * vp;
+  if (order == 2) f = f + a2 * (vp * vp);
+  return f - delta_pt;
+}
+
 __global__ void k_kappa(int W, int H, int order, double a0, double a1, double a2, double cs,
                         double sn, double delta_pt, int32_t* __restrict__ kappa) {
   int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -33,13 +47,17 @@ __global__ void k_kappa(int W, int H, int order, double a0, double a1, double a2
   double uc = (double)(W - 1) * 0.5, vc = (double)(H - 1) * 0.5;
   double t1 = ((double)v - vc) * cs;
   double best = 1e300;
-  for (int x = lane; x < W; x += 32) {
-    double t2 = ((double)x - uc) * sn;
-    double vp = (t1 - t2) + vc;
-    double f = a0 + a1 * vp;
-    if (order == 2) f = f + a2 * (vp * vp);
-    f = f - delta_pt;
-    best = f < best ? f : best;
+  if (lane < 2) best = road_minus(t1, uc, vc, sn, order, a0, a1, a2, delta_pt, lane == 0 ? 0 : W - 1);
+  if (order == 2 && a2 > 0.0 && sn != 0.0) {
+    double xs = uc + ((t1 + vc) + a1 / (2.0 * a2)) / sn;  // column of the vertex vp = -a1 / (2 a2)
+    if (xs > -64.0 && xs < (double)W + 64.0) {
+      int xc = (int)floor(xs);
+      for (int x = xc - 31 + 2 * lane; x <= xc - 30 + 2 * lane; ++x)
+        if (x >= 0 && x < W) {
+          double f = road_minus(t1, uc, vc, sn, order, a0, a1, a2, delta_pt, x);
+          best = f < best ? f : best;
+        }
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
     double other = __shfl_xor_sync(kFull, best, o);
@@ -185,7 +203,20 @@ __global__ void k_to_natural(const uint8_t* __restrict__ in, size_t n_groups,
 // ----------------------------------------------------------------------------- Eq. (8)
 constexpr int kAggWarps = 4;
 
-constexpr int kPrefetch = 8;  // cost loads in flight per lane (steps ahead)
+constexpr int kStages = 16;  // per-warp shared-memory ring of cost rows: kStages - 1 steps in flight
+
+// Asynchronous 16-byte copy global -> shared (cp.async, L2 only); src_bytes = 0 writes zeros and
+// reads nothing.
+__device__ __forceinline__ void cp_async16(uint32_t smem, const void* gmem, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem), "l"(gmem),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 // Every line of direction (dx, dy) is walked by a step index s; the pixel at step s moves by a
 // constant byte stride through the [H][W][D] volumes, and the line lies inside the image for one
@@ -239,15 +270,18 @@ __device__ __forceinline__ LineWalk line_walk(int dx, int dy, int W, int H, int 
   return w;
 }
 
+// Directions are packed 4 bits each into `dirs` (bits 4r..4r+3 of direction r): dx + 1 in the
+// low two bits, dy + 1 in the high two.
 template <int G>
-__global__ void __launch_bounds__(kAggWarps * 32, 5) k_aggregate(const uint8_t* __restrict__ cost,
+__global__ void __launch_bounds__(kAggWarps * 32, 6) k_aggregate(const uint8_t* __restrict__ cost,
                                                                  uint8_t* __restrict__ out, int W,
-                                                                 int H, int D, DirSet dirs,
+                                                                 int H, int D, uint32_t dirs,
                                                                  uint32_t P1x2, uint32_t K21x2,
                                                                  size_t vol_bytes) {
   constexpr int LPW = 32 / G;  // lines per warp
   const int r = blockIdx.y;
-  const int dx = dirs.dx[r], dy = dirs.dy[r];
+  const uint32_t code = (dirs >> (4 * r)) & 0xfu;
+  const int dx = (int)(code & 3u) - 1, dy = (int)(code >> 2) - 1;
   const int nlines = dy == 0 ? H : (dx == 0 ? W : W + H - 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane % G;
@@ -259,30 +293,46 @@ __global__ void __launch_bounds__(kAggWarps * 32, 5) k_aggregate(const uint8_t* 
   const uint8_t* csrc = cost + 16 * g;
   uint8_t* dst = out + (size_t)r * vol_bytes + 16 * g;
 
+  // State: L of the previous pixel on the line (the oracle's normalised value) and its minimum
+  // mp over all disparities, replicated in both u16 halves.  A line starts from L = 0, mp = 0,
+  // which makes its first pixel's L equal to the cost.
   uint32_t N[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) N[j] = 0;
+  uint32_t mp = 0;
 
-  uint4 ring[kPrefetch];
+  // Cost rows arrive through a per-warp ring in shared memory: stage k of lane `lane` holds the
+  // 16 cost bytes of one step.  Step s is read from stage s % kStages after waiting for its copy;
+  // the copy for step s + kStages - 1 then goes into the stage read one step earlier.
+  extern __shared__ uint4 s_ring[];
+  uint4* ring = s_ring + (size_t)warp * kStages * 32 + lane;
+  const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
   long long pf_off = lw.off0;  // offset of the step being prefetched
 #pragma unroll
-  for (int k = 0; k < kPrefetch; ++k) {
-    ring[k] = make_uint4(0, 0, 0, 0);
-    if (k >= lw.s_first && k <= lw.s_last) ring[k] = __ldg(reinterpret_cast<const uint4*>(csrc + pf_off));
+  for (int k = 0; k < kStages - 1; ++k) {
+    const bool in = k >= lw.s_first && k <= lw.s_last;
+    cp_async16(ring_s + k * 32 * 16, csrc + (in ? pf_off : 0), in ? 16u : 0u);
+    cp_async_commit();
     pf_off += lw.delta;
   }
   long long st_off = lw.off0;  // offset of the current step
-  for (int s0 = 0; s0 < lw.nsteps; s0 += kPrefetch) {
+  for (int s0 = 0; s0 < lw.nsteps; s0 += kStages) {
 #pragma unroll
-    for (int k = 0; k < kPrefetch; ++k) {
+    for (int k = 0; k < kStages; ++k) {
       const int s = s0 + k;
       if (s >= lw.nsteps) break;  // warp-uniform
       const bool act = s >= lw.s_first && s <= lw.s_last;
-      const uint32_t raw[4] = {ring[k].x, ring[k].y, ring[k].z, ring[k].w};
-      const int sp = s + kPrefetch;
-      if (sp >= lw.s_first && sp <= lw.s_last)
-        ring[k] = __ldg(reinterpret_cast<const uint4*>(csrc + pf_off));
-      pf_off += lw.delta;
+      cp_async_wait<kStages - 2>();  // the copy of step s is complete
+      const uint4 rv = ring[k * 32];
+      const uint32_t raw[4] = {rv.x, rv.y, rv.z, rv.w};
+      {
+        const int sp = s + kStages - 1;
+        const bool in = sp >= lw.s_first && sp <= lw.s_last;
+        cp_async16(ring_s + ((k + kStages - 1) % kStages) * 32 * 16, csrc + (in ? pf_off : 0),
+                   in ? 16u : 0u);
+        cp_async_commit();
+        pf_off += lw.delta;
+      }
       // neighbours across the lane boundaries of this line's lane group
       uint32_t prevHi = kBig2, nextLo = kBig2;
       if constexpr (G > 1) {
@@ -293,18 +343,22 @@ __global__ void __launch_bounds__(kAggWarps * 32, 5) k_aggregate(const uint8_t* 
       }
       const uint32_t left0 = __byte_perm(prevHi, N[7], 0x5432);
       const uint32_t right7 = __byte_perm(N[0], nextLo, 0x5432);
+      const uint32_t K = mp + K21x2;  // m + P2 - P1 in both halves (no carry: all < 2^15)
       uint32_t Lw[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         uint32_t lft = j == 0 ? left0 : N[j - 1];
         uint32_t rgt = j == 7 ? right7 : N[j + 1];
-        uint32_t t = __vimin3_u16x2(lft, rgt, K21x2);
+        // min(L[d-1], L[d+1], m + P2 - P1) + P1 against L[d]: the minimum of Eq. (8)
+        uint32_t t = __vimin3_u16x2(lft, rgt, K);
         t = __viaddmin_u16x2(t, P1x2, N[j]);
         uint32_t c = __byte_perm(raw[j >> 1], 0, (j & 1) ? 0x4342 : 0x4140);
-        Lw[j] = __vadd2(t, c);
+        // c + t - m in one 32-bit three-input add: each half of t is >= m, so no borrow or
+        // carry crosses between the halves
+        Lw[j] = t + c - mp;
       }
-      uint32_t m = __vminu2(__vminu2(__vminu2(Lw[0], Lw[1]), __vminu2(Lw[2], Lw[3])),
-                            __vminu2(__vminu2(Lw[4], Lw[5]), __vminu2(Lw[6], Lw[7])));
+      uint32_t m = __vimin3_u16x2(__vimin3_u16x2(Lw[0], Lw[1], Lw[2]),
+                                  __vimin3_u16x2(Lw[3], Lw[4], Lw[5]), __vminu2(Lw[6], Lw[7]));
       m = __vminu2(m, __byte_perm(m, m, 0x1032));  // both halves = min of the two halves
 #pragma unroll
       for (int o = 1; o < G; o <<= 1) m = __vminu2(m, __shfl_xor_sync(kFull, m, o, G));
@@ -316,14 +370,17 @@ __global__ void __launch_bounds__(kAggWarps * 32, 5) k_aggregate(const uint8_t* 
         w.w = __byte_perm(Lw[6], Lw[7], 0x6420);
         __stcs(reinterpret_cast<uint4*>(dst + st_off), w);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) N[j] = __vsub2(Lw[j], m);
+        for (int j = 0; j < 8; ++j) N[j] = Lw[j];
+        mp = m;
       } else {
 #pragma unroll
         for (int j = 0; j < 8; ++j) N[j] = 0;
+        mp = 0;
       }
       st_off += lw.delta;
     }
   }
+  cp_async_wait<0>();  // no copy may still be in flight when the warp exits
 }
 
 // ------------------------------------------------------------- volume sums and Eq. (9)
@@ -533,13 +590,25 @@ void launch_aggregate(cudaStream_t s, const uint8_t* cost_il, int W, int H, int 
   }
   int lines_per_block = kAggWarps * (32 / G);
   dim3 grid((maxlines + lines_per_block - 1) / lines_per_block, dirs.n);
+  const size_t smem = (size_t)kAggWarps * kStages * 32 * sizeof(uint4);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_aggregate<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_aggregate<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_aggregate<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_aggregate<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set = true;
+  }
   uint32_t P1x2 = (uint32_t)P1 * 0x10001u;
   uint32_t K21x2 = (uint32_t)(P2 - P1) * 0x10001u;
+  uint32_t packed = 0;
+  for (int r = 0; r < dirs.n; ++r)
+    packed |= ((uint32_t)(dirs.dx[r] + 1) | ((uint32_t)(dirs.dy[r] + 1) << 2)) << (4 * r);
   switch (G) {
-    case 2: k_aggregate<2><<<grid, kAggWarps * 32, 0, s>>>(cost_il, out, W, H, D, dirs, P1x2, K21x2, vol_bytes); break;
-    case 4: k_aggregate<4><<<grid, kAggWarps * 32, 0, s>>>(cost_il, out, W, H, D, dirs, P1x2, K21x2, vol_bytes); break;
-    case 8: k_aggregate<8><<<grid, kAggWarps * 32, 0, s>>>(cost_il, out, W, H, D, dirs, P1x2, K21x2, vol_bytes); break;
-    case 16: k_aggregate<16><<<grid, kAggWarps * 32, 0, s>>>(cost_il, out, W, H, D, dirs, P1x2, K21x2, vol_bytes); break;
+    case 2: k_aggregate<2><<<grid, kAggWarps * 32, smem, s>>>(cost_il, out, W, H, D, packed, P1x2, K21x2, vol_bytes); break;
+    case 4: k_aggregate<4><<<grid, kAggWarps * 32, smem, s>>>(cost_il, out, W, H, D, packed, P1x2, K21x2, vol_bytes); break;
+    case 8: k_aggregate<8><<<grid, kAggWarps * 32, smem, s>>>(cost_il, out, W, H, D, packed, P1x2, K21x2, vol_bytes); break;
+    case 16: k_aggregate<16><<<grid, kAggWarps * 32, smem, s>>>(cost_il, out, W, H, D, packed, P1x2, K21x2, vol_bytes); break;
     default: break;  // the API admits D in {32, 64, 128, 256} only
   }
 }
