@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-pair mixed batch")
     ap.add_argument("--size", default=None,
                     help="WxH of a smaller road for profiling captures (not a benchmark line)")
     return ap.parse_args()
@@ -165,6 +166,62 @@ def run_reference(args, rank, world):
                          "sample": sample},
         "e2e": {"value": val, "unit": "Mdisp/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+def bench_batch(B, torch, synth, n_pairs=64, steps=5, seq_steps=2):
+    """The mixed batch: n pairs with resolutions from {640x480, 1280x720, 1920x1080} and disparity
+    ranges from {32, 64, 128}; one pd_sgm_batch call (CUDA graph, autotuned) against n
+    sequential pd_sgm calls, both timed with CUDA events on the library stream, L2 flushed before
+    every timed call."""
+    scenes = synth.mixed_batch(n_pairs)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(stream):
+        ctx = B.Context(torch.cuda.current_device(), stream=stream)
+        B.pd_batch_config(ctx, use_graph=True, autotune=True)
+        items = []
+        for sc, D in scenes:
+            left, right = synth.render(sc)
+            items.append((torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda(),
+                          B.RoadModel.make(*synth.true_model(sc)), D))
+        disp = sum(it[0].shape[0] * it[0].shape[1] * it[3] for it in items)
+        batch = B.make_batch(ctx, items)
+        params = B.default_params()
+        for _ in range(3):  # autotune, capture, replay
+            B.pd_sgm_batch(ctx, batch, params)
+        stream.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.pd_sgm_batch(ctx, batch, params)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        outs = [B.pd_sgm(ctx, it[0], it[1], it[2], B.default_params(D=it[3])) for it in items]
+        stream.synchronize()
+        same = all(torch.equal(o[1], b["d_int"]) and torch.equal(o[2], b["D1"])
+                   for o, b in zip(outs, batch[1]))
+        seq = []
+        for _ in range(seq_steps):
+            flush.fill_(2)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for it, o in zip(items, outs):
+                B.pd_sgm(ctx, it[0], it[1], it[2], B.default_params(D=it[3]), kappa=o[0],
+                         d_int=o[1], D1=o[2])
+            e1.record(stream)
+            e1.synchronize()
+            seq.append(e0.elapsed_time(e1))
+        ctx.close()
+    tb, ts = statistics.median(ms), statistics.median(seq)
+    return {"workload": "%d mixed pairs {640x480,1280x720,1920x1080} x D {32,64,128}, 8 paths" % n_pairs,
+            "batched_ms": tb, "batched_frames_per_s": n_pairs / (tb * 1e-3),
+            "batched_Mdisp_s": disp / (tb * 1e-3) / 1e6,
+            "sequential_ms": ts, "sequential_frames_per_s": n_pairs / (ts * 1e-3),
+            "sequential_Mdisp_s": disp / (ts * 1e-3) / 1e6, "speedup": ts / tb,
+            "identical_to_sequential": bool(same)}
 
 
 def main():
@@ -297,6 +354,10 @@ def main():
                              "peak_source": "64 int instr/clk/SM (microbenchmark) x 2 u16 lanes "
                                             "x 152 SMs x %.0f MHz" % sm_max}}
 
+    batch = None
+    if not args.no_batch and not args.size:
+        batch = bench_batch(B, torch, synth)
+
     cpu = None
     if not args.no_cpu_baseline:
         import oracle
@@ -318,7 +379,7 @@ def main():
                    "stage_ms": {k: prof[k] / calls for k in ("prep_ms", "aggregate_ms",
                                                             "disparity_ms", "transform_ms",
                                                             "superpixel_ms", "mask_ms")},
-                   "wall_s": wall},
+                   "wall_s": wall, "batch64": batch},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": prof["launches"], "clocks": clocks,
     }

@@ -253,6 +253,41 @@ pd_status pd_profile_enable(pd_ctx* ctx, int on);
  * recording. */
 pd_status pd_profile_read(pd_ctx* ctx, pd_profile* out);
 
+/* ------------------------------------------------- batched form (an extension of the paper) */
+
+/* One stereo pair of a batch (host struct; the pointers are device pointers). */
+typedef struct {
+  const uint8_t* left;
+  const uint8_t* right;
+  int W, H;
+  size_t pitch;
+  int D;                /* 32, 64, 128 or 256, chosen per pair */
+  int pad;
+  pd_road_model model;  /* the pair's road model for the warp, by value */
+  int32_t* kappa;       /* [H] row shifts, may be NULL */
+  int16_t* d_int;       /* [H][W] */
+  float* D1;            /* [H][W] */
+} pd_pair;
+
+/* Options of pd_sgm_batch on this context:
+ *  - scratch_budget_bytes: device scratch the batch may use; pairs are processed in consecutive
+ *    waves that fit it (0 keeps the default, 32 GiB).  A pair larger than the budget runs alone.
+ *  - use_graph != 0: the launch sequence of a batch is captured into a CUDA graph the first time a
+ *    batch of the same shape (sizes, D, parameters) is run on a non-default stream and replayed on
+ *    later calls with any buffers.
+ *  - autotune != 0 (default): on the first batch of a shape, the persistent aggregation kernel is
+ *    timed with 2, 4 and 8 warps per block and the fastest is kept for that shape.  Every choice
+ *    gives identical results. */
+pd_status pd_batch_config(pd_ctx* ctx, size_t scratch_budget_bytes, int use_graph, int autotune);
+
+/* Sec. II-A and II-B for n pairs of any sizes and disparity ranges with one launch per stage and
+ * wave; the aggregation is one persistent launch whose warps take line groups of all pairs from a
+ * shared counter, longest lines first.  Results are identical to n pd_sgm calls.
+ * pairs: host array of n descriptors; params: host (paths, P1, P2, lr_tol, delta_pt are used; D
+ * is per pair).  The call returns after enqueueing; it waits for the previous batch on this
+ * context to pass its table upload before reusing the host staging buffer. */
+pd_status pd_sgm_batch(pd_ctx* ctx, const pd_pair* pairs, int n, const pd_params* params);
+
 /* -------------------------------------------------------------------------- whole path */
 
 /* pd_sgm, pd_transform, pd_superpixels and pd_pothole_mask in sequence on one stream.

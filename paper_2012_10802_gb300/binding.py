@@ -70,6 +70,12 @@ class Profile(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
 
 
+class Pair(C.Structure):
+    _fields_ = [("left", C.c_void_p), ("right", C.c_void_p), ("W", C.c_int), ("H", C.c_int),
+                ("pitch", C.c_size_t), ("D", C.c_int), ("pad", C.c_int), ("model", RoadModel),
+                ("kappa", C.c_void_p), ("d_int", C.c_void_p), ("D1", C.c_void_p)]
+
+
 _P, _i, _z, _f = C.c_void_p, C.c_int, C.c_size_t, C.c_float
 SIGNATURES = {
     "pd_create": [C.POINTER(C.c_void_p), _i, _P],
@@ -90,6 +96,8 @@ SIGNATURES = {
     "pd_run_pipeline": [_P, _P, _P, _i, _i, _z, C.POINTER(RoadModel), C.POINTER(Params),
                         C.POINTER(Outputs), C.POINTER(StageTimes)],
     "pd_transform_noalloc": [_P, _i, _i, _i, _f, _P, _P, _P],
+    "pd_batch_config": [_P, C.c_size_t, _i, _i],
+    "pd_sgm_batch": [_P, C.POINTER(Pair), _i, C.POINTER(Params)],
     "pd_profile_enable": [_P, _i],
     "pd_profile_read": [_P, C.POINTER(Profile)],
 }
@@ -335,3 +343,33 @@ def pd_transform_noalloc(D1, order, delta_dt, fitted, D2, stream=None):
         stream = torch.cuda.current_stream(D1.device)
     return lib().pd_transform_noalloc(_ptr(D1), W, H, order, float(delta_dt), _ptr(fitted),
                                       _ptr(D2), C.c_void_p(stream.cuda_stream))
+
+
+def pd_batch_config(ctx, scratch_budget_bytes=0, use_graph=False, autotune=True):
+    ctx.check(lib().pd_batch_config(ctx.h, int(scratch_budget_bytes), 1 if use_graph else 0,
+                                    1 if autotune else 0))
+
+
+def make_batch(ctx, items):
+    """items: list of (left, right, RoadModel, D).  Allocates the outputs; returns (Pair array,
+    list of dicts with kappa / d_int / D1 tensors)."""
+    arr = (Pair * len(items))()
+    outs = []
+    for k, (left, right, model, D) in enumerate(items):
+        H, W = left.shape
+        o = {"kappa": ctx.empty((H,), torch.int32), "d_int": ctx.empty((H, W), torch.int16),
+             "D1": ctx.empty((H, W), torch.float32)}
+        arr[k].left = left.data_ptr()
+        arr[k].right = right.data_ptr()
+        arr[k].W, arr[k].H, arr[k].pitch, arr[k].D = W, H, W, int(D)
+        arr[k].model = model
+        arr[k].kappa = o["kappa"].data_ptr()
+        arr[k].d_int = o["d_int"].data_ptr()
+        arr[k].D1 = o["D1"].data_ptr()
+        outs.append(o)
+    return arr, outs
+
+
+def pd_sgm_batch(ctx, batch, params):
+    arr, _ = batch
+    ctx.check(lib().pd_sgm_batch(ctx.h, arr, len(arr), C.byref(params)))

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpothole.so")
-SOURCES = ["api.cu", "sgm.cu", "dt.cu", "detect.cu"]
+SOURCES = ["api.cu", "sgm.cu", "dt.cu", "detect.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC,-O2",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
@@ -35,7 +35,9 @@ def _stale(target, deps):
 
 def build(force=False, verbose=False, extra=()):
     os.makedirs(OUT, exist_ok=True)
-    headers = [os.path.join(CSRC, "common.cuh"), os.path.join(ROOT, "include", "pothole.h")]
+    headers = [os.path.join(CSRC, "common.cuh"), os.path.join(CSRC, "sgm_body.cuh"),
+               os.path.join(CSRC, "batch.cuh"),
+               os.path.join(ROOT, "include", "pothole.h")]
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)

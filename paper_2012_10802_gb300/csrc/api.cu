@@ -6,6 +6,11 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <map>
+#include <vector>
+
+#include "batch.cuh"
 #include "common.cuh"
 
 namespace pd {
@@ -224,6 +229,270 @@ pd_status transform_enqueue(pd_ctx* ctx, const float* D1, int W, int H, int orde
 
 }  // namespace
 
+
+// ------------------------------------------------------------------------- batched SGM
+
+namespace {
+
+struct WavePlan {
+  int first, count;
+  size_t table_off, table_bytes;  // within the table region
+  size_t pairs_off, starts_off[kBatchStages], segs_off, counter_off;
+  int nseg, ntasks;
+  int total[kBatchStages];
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Launches the recorded waves (table upload first).
+void batch_enqueue(pd_ctx* ctx, const std::vector<WavePlan>& waves, char* table_dev,
+                   size_t table_bytes, const pd_params* p, int agg_warps, int agg_blocks) {
+  cudaStream_t s = ctx->stream;
+  cudaMemcpyAsync(table_dev, ctx->pinned, table_bytes, cudaMemcpyHostToDevice, s);
+  for (const WavePlan& w : waves) {
+    BatchWaveDev d;
+    char* base = table_dev + w.table_off;
+    d.pairs = reinterpret_cast<const BatchPair*>(base + w.pairs_off);
+    for (int k = 0; k < kBatchStages; ++k) d.starts[k] = reinterpret_cast<const int*>(base + w.starts_off[k]);
+    d.segs = reinterpret_cast<const BatchSegment*>(base + w.segs_off);
+    d.counter = reinterpret_cast<unsigned int*>(base + w.counter_off);
+    d.npairs = w.count;
+    d.nseg = w.nseg;
+    d.ntasks = w.ntasks;
+    for (int k = 0; k < kBatchStages; ++k) d.total[k] = w.total[k];
+    launch_batch_wave(s, d, p->P1, p->P2, p->lr_tol, p->paths, agg_warps, agg_blocks);
+  }
+}
+
+}  // namespace
+
+extern "C" pd_status pd_batch_config(pd_ctx* ctx, size_t scratch_budget_bytes, int use_graph,
+                                     int autotune) {
+  if (!ctx) return PD_ERR_INVALID_ARG;
+  if (scratch_budget_bytes) ctx->batch_budget = scratch_budget_bytes;
+  ctx->batch_graph = use_graph != 0;
+  ctx->batch_autotune = autotune != 0;
+  return PD_OK;
+}
+
+extern "C" pd_status pd_sgm_batch(pd_ctx* ctx, const pd_pair* pairs, int n, const pd_params* p) {
+  PD_TRY(begin(ctx));
+  PD_TRY(check_sgm_params(ctx, p));
+  PD_REQUIRE(pairs != nullptr && n >= 1 && n <= 4096, "need 1..4096 pairs (got %d)", n);
+  std::vector<size_t> need(n);
+  for (int i = 0; i < n; ++i) {
+    const pd_pair& q = pairs[i];
+    PD_TRY(check_image(ctx, q.W, q.H, q.pitch));
+    PD_TRY(check_model(ctx, &q.model));
+    PD_REQUIRE(pow2_d(q.D), "pair %d: D = %d must be 32, 64, 128 or 256", i, q.D);
+    PD_REQUIRE(q.left && q.right && q.d_int && q.D1, "pair %d: NULL image or output", i);
+    need[i] = align256(sgm_scratch_bytes(q.W, q.H, q.D, p->paths));
+  }
+  // waves of consecutive pairs within the scratch budget
+  std::vector<WavePlan> waves;
+  size_t scratch_region = 0;
+  for (int i = 0; i < n;) {
+    WavePlan w{};
+    w.first = i;
+    size_t used = 0;
+    while (i < n && (used == 0 || used + need[i] <= ctx->batch_budget)) used += need[i++];
+    w.count = i - w.first;
+    scratch_region = std::max(scratch_region, used);
+    waves.push_back(w);
+  }
+  // table layout of every wave
+  size_t table_bytes = 0;
+  for (WavePlan& w : waves) {
+    w.table_off = table_bytes;
+    size_t o = 0;
+    w.pairs_off = o;
+    o = align256(o + sizeof(BatchPair) * w.count);
+    for (int k = 0; k < kBatchStages; ++k) {
+      w.starts_off[k] = o;
+      o = align256(o + sizeof(int) * (w.count + 1));
+    }
+    w.segs_off = o;
+    o = align256(o + sizeof(BatchSegment) * w.count * p->paths);
+    w.counter_off = o;
+    o = align256(o + sizeof(unsigned int));
+    w.table_bytes = o;
+    table_bytes += o;
+  }
+  PD_TRY(ensure_ws(ctx, table_bytes + scratch_region));
+  char* table_dev = static_cast<char*>(ctx->ws);
+  char* scratch = table_dev + align256(table_bytes);
+  // the previous batch must have consumed the staging buffer before it is rewritten
+  if (ctx->batch_inflight) {
+    PD_TRY(cuda_ok(ctx, cudaEventSynchronize(ctx->batch_done), "pd_sgm_batch"));
+    ctx->batch_inflight = false;
+  }
+  if (ctx->pinned_bytes < table_bytes) {
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    ctx->pinned = nullptr;
+    ctx->pinned_bytes = 0;
+    size_t want = table_bytes + (table_bytes >> 2) + 4096;
+    PD_TRY(cuda_ok(ctx, cudaHostAlloc(&ctx->pinned, want, cudaHostAllocDefault), "pinned staging"));
+    ctx->pinned_bytes = want;
+  }
+  if (!ctx->batch_done)
+    PD_TRY(cuda_ok(ctx, cudaEventCreateWithFlags(&ctx->batch_done, cudaEventDisableTiming),
+                   "cudaEventCreate"));
+  static const int kDx[8] = {1, -1, 0, 0, 1, -1, 1, -1};
+  static const int kDy[8] = {0, 0, 1, -1, 1, -1, -1, 1};
+  std::vector<long long> sig = {n, p->paths, p->P1, p->P2, p->lr_tol,
+                                (long long)(double)p->delta_pt * 1000000};
+  for (WavePlan& w : waves) {
+    char* hbase = static_cast<char*>(ctx->pinned) + w.table_off;
+    BatchPair* bp = reinterpret_cast<BatchPair*>(hbase + w.pairs_off);
+    int* starts[kBatchStages];
+    for (int k = 0; k < kBatchStages; ++k) {
+      starts[k] = reinterpret_cast<int*>(hbase + w.starts_off[k]);
+      starts[k][0] = 0;
+    }
+    struct Seg {
+      BatchSegment s;
+      int ntasks, nsteps;
+    };
+    std::vector<Seg> segs;
+    size_t off = 0;
+    for (int j = 0; j < w.count; ++j) {
+      const pd_pair& q = pairs[w.first + j];
+      SgmScratch sc = sgm_carve(scratch + off, q.W, q.H, q.D, p->paths);
+      off += need[w.first + j];
+      BatchPair& b = bp[j];
+      b.left = q.left;
+      b.right = q.right;
+      b.pitch = q.pitch;
+      b.kappa = q.kappa ? q.kappa : sc.kappa;
+      b.d_int = q.d_int;
+      b.D1 = q.D1;
+      b.cl = sc.cl;
+      b.cr = sc.cr;
+      b.cost = sc.cost;
+      b.vols = sc.vols;
+      b.dsub = sc.dsub;
+      b.rkeys = sc.rkeys;
+      b.vol_bytes = (size_t)q.W * q.H * q.D;
+      b.a0 = q.model.a[0];
+      b.a1 = q.model.a[1];
+      b.a2 = q.model.a[2];
+      b.cs = cos(q.model.roll);
+      b.sn = sin(q.model.roll);
+      b.delta_pt = (double)p->delta_pt;
+      b.W = q.W;
+      b.H = q.H;
+      b.D = q.D;
+      b.order = q.model.order;
+      int cnt[kBatchStages];
+      batch_stage_blocks(q.W, q.H, q.D, cnt);
+      for (int k = 0; k < kBatchStages; ++k) starts[k][j + 1] = starts[k][j] + cnt[k];
+      const int lpw = batch_lines_per_warp(q.D);
+      for (int r = 0; r < p->paths; ++r) {
+        const int dx = kDx[r], dy = kDy[r];
+        const int nlines = dy == 0 ? q.H : (dx == 0 ? q.W : q.W + q.H - 1);
+        const int nsteps = dy == 0 ? q.W : (dx == 0 ? q.H : std::min(q.W, q.H));
+        Seg sg;
+        sg.s = BatchSegment{0, j, r, dx, dy, 0};
+        sg.ntasks = (nlines + lpw - 1) / lpw;
+        sg.nsteps = nsteps;
+        segs.push_back(sg);
+      }
+      sig.insert(sig.end(), {q.W, q.H, q.D, (long long)q.pitch});
+    }
+    std::stable_sort(segs.begin(), segs.end(),
+                     [](const Seg& a, const Seg& b) { return a.nsteps > b.nsteps; });
+    BatchSegment* hs = reinterpret_cast<BatchSegment*>(hbase + w.segs_off);
+    int first = 0;
+    for (size_t k = 0; k < segs.size(); ++k) {
+      hs[k] = segs[k].s;
+      hs[k].first = first;
+      first += segs[k].ntasks;
+    }
+    w.nseg = (int)segs.size();
+    w.ntasks = first;
+    for (int k = 0; k < kBatchStages; ++k) w.total[k] = starts[k][w.count];
+    *reinterpret_cast<unsigned int*>(hbase + w.counter_off) = 0;
+  }
+  // persistent aggregation: block shape from the tuning cache (4 warps until tuned)
+  auto* tuned = static_cast<std::map<std::vector<long long>, int>*>(ctx->tuned);
+  if (!tuned) ctx->tuned = tuned = new std::map<std::vector<long long>, int>();
+  int agg_warps = 4;
+  const bool known = tuned->count(sig) != 0;
+  if (known) agg_warps = (*tuned)[sig];
+  static bool smem_attr = false;
+  if (!smem_attr) {  // the largest block (8 warps) sets the dynamic shared memory limit once
+    batch_max_blocks_per_sm(8);
+    smem_attr = true;
+  }
+  auto blocks_for = [&](int warps) { return ctx->sm_count * std::max(1, batch_max_blocks_per_sm(warps)); };
+  cudaStream_t s = ctx->stream;
+  if (ctx->batch_autotune && !known) {
+    // run the batch once, then time the aggregation of the first wave with each block shape
+    batch_enqueue(ctx, waves, table_dev, table_bytes, p, agg_warps, blocks_for(agg_warps));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int wc : {2, 4, 8}) {
+      const WavePlan& w = waves[0];
+      BatchWaveDev d;
+      char* base = table_dev + w.table_off;
+      d.pairs = reinterpret_cast<const BatchPair*>(base + w.pairs_off);
+      for (int k = 0; k < kBatchStages; ++k) d.starts[k] = reinterpret_cast<const int*>(base + w.starts_off[k]);
+      d.segs = reinterpret_cast<const BatchSegment*>(base + w.segs_off);
+      d.counter = reinterpret_cast<unsigned int*>(base + w.counter_off);
+      d.npairs = w.count;
+      d.nseg = w.nseg;
+      d.ntasks = w.ntasks;
+      cudaEventRecord(e0, s);
+      launch_batch_aggregate_only(s, d, p->P1, p->P2, wc, blocks_for(wc));
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        agg_warps = wc;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    (*tuned)[sig] = agg_warps;
+    PD_TRY(launched(ctx, "pd_sgm_batch (tuning)"));
+    cudaEventRecord(ctx->batch_done, s);
+    ctx->batch_inflight = true;
+    return PD_OK;
+  }
+  const int agg_blocks = blocks_for(agg_warps);
+  if (ctx->batch_graph && s != nullptr) {
+    // a captured graph holds the scratch, staging and stream addresses: they are part of its key
+    std::vector<long long> gkey = sig;
+    gkey.insert(gkey.end(), {(long long)(uintptr_t)ctx->ws, (long long)(uintptr_t)ctx->pinned,
+                             (long long)(uintptr_t)s, agg_warps});
+    auto* gsig = static_cast<std::vector<long long>*>(ctx->graph_sig);
+    if (!ctx->graph_exec || !gsig || *gsig != gkey) {
+      if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+      ctx->graph_exec = nullptr;
+      cudaGraph_t g = nullptr;
+      PD_TRY(cuda_ok(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture"));
+      batch_enqueue(ctx, waves, table_dev, table_bytes, p, agg_warps, agg_blocks);
+      PD_TRY(cuda_ok(ctx, cudaStreamEndCapture(s, &g), "capture"));
+      cudaError_t e = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+      cudaGraphDestroy(g);
+      PD_TRY(cuda_ok(ctx, e, "cudaGraphInstantiate"));
+      delete gsig;
+      ctx->graph_sig = new std::vector<long long>(gkey);
+    }
+    PD_TRY(cuda_ok(ctx, cudaGraphLaunch(ctx->graph_exec, s), "cudaGraphLaunch"));
+  } else {
+    batch_enqueue(ctx, waves, table_dev, table_bytes, p, agg_warps, agg_blocks);
+  }
+  PD_TRY(launched(ctx, "pd_sgm_batch"));
+  cudaEventRecord(ctx->batch_done, s);
+  ctx->batch_inflight = true;
+  return PD_OK;
+}
+
 // ============================================================================== C ABI
 
 extern "C" {
@@ -261,6 +530,11 @@ pd_status pd_destroy(pd_ctx* ctx) {
         if (e) cudaEventDestroy(e);
     delete[] ctx->recs;
   }
+  if (ctx->batch_done) cudaEventDestroy(ctx->batch_done);
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  delete static_cast<std::vector<long long>*>(ctx->graph_sig);
+  delete static_cast<std::map<std::vector<long long>, int>*>(ctx->tuned);
   delete ctx;
   return PD_OK;
 }

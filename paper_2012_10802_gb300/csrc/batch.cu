@@ -1,0 +1,194 @@
+// Batched Sec. II-A / II-B over many stereo pairs of different sizes and disparity ranges.
+//
+// One launch per stage covers every pair of a wave: blocks find their pair in a prefix table of
+// per-pair block counts and run the same block bodies as the single-pair kernels (sgm_body.cuh),
+// so the results are identical to one pd_sgm call per pair.  The aggregation is one persistent
+// launch: each warp repeatedly takes the next task (a group of lines of one pair and one
+// direction) from an atomic counter over a task list ordered longest-first, so short and long
+// lines of all pairs share the GPU.  No kernel waits on another block.
+#include "batch.cuh"
+#include "sgm_body.cuh"
+
+namespace pd {
+
+namespace {
+
+using namespace body;
+
+__device__ __forceinline__ int find_pair(const int* __restrict__ starts, int npairs, int b) {
+  int lo = 0, hi = npairs - 1;  // largest i with starts[i] <= b
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (starts[mid] <= b)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void k_kappa_b(const BatchPair* __restrict__ pairs, const int* __restrict__ starts,
+                          int npairs) {
+  const int i = find_pair(starts, npairs, blockIdx.x);
+  const BatchPair& p = pairs[i];
+  const int v = (blockIdx.x - starts[i]) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (v >= p.H) return;
+  kappa_row(p.W, p.H, p.order, p.a0, p.a1, p.a2, p.cs, p.sn, p.delta_pt, p.kappa, v,
+            threadIdx.x & 31);
+}
+
+// Blocks [0, total) census the left images, [total, 2 total) the row-shifted right images.
+__global__ void k_census_b(const BatchPair* __restrict__ pairs, const int* __restrict__ starts,
+                           int npairs, int total) {
+  const bool right = (int)blockIdx.x >= total;
+  const int b = right ? blockIdx.x - total : blockIdx.x;
+  const int i = find_pair(starts, npairs, b);
+  const BatchPair& p = pairs[i];
+  const int t = b - starts[i];
+  const int tx = (p.W + kCT_W - 1) / kCT_W;
+  census_tile(right ? p.right : p.left, p.W, p.H, p.pitch, right ? p.kappa : nullptr,
+              right ? p.cr : p.cl, t % tx, t / tx);
+}
+
+__global__ void __launch_bounds__(kCostThreads) k_cost_b(const BatchPair* __restrict__ pairs,
+                                                         const int* __restrict__ starts,
+                                                         int npairs) {
+  const int i = find_pair(starts, npairs, blockIdx.x);
+  const BatchPair& p = pairs[i];
+  const int b = blockIdx.x - starts[i];
+  const int P = kCostThreads / (p.D >> 4);
+  const int nbx = (p.W + P - 1) / P;
+  cost_il_block(p.cl, p.cr, p.W, p.D, p.cost, b % nbx, b / nbx);
+}
+
+__global__ void k_fill_b(const BatchPair* __restrict__ pairs, const int* __restrict__ starts,
+                         int npairs) {
+  const int i = find_pair(starts, npairs, blockIdx.x);
+  const BatchPair& p = pairs[i];
+  const size_t N = (size_t)p.W * p.H;
+  for (size_t k = (size_t)(blockIdx.x - starts[i]) * blockDim.x + threadIdx.x; k < N;
+       k += (size_t)(starts[i + 1] - starts[i]) * blockDim.x)
+    p.rkeys[k] = 0xffffffffu;
+}
+
+// Persistent aggregation.  Task t belongs to the segment s with seg[s].first <= t; its lines are
+// first = (t - seg[s].first) * 32 / G onwards.
+__global__ void __launch_bounds__(256) k_aggregate_b(const BatchPair* __restrict__ pairs,
+                                                     const BatchSegment* __restrict__ seg,
+                                                     int nseg, int ntasks,
+                                                     unsigned int* __restrict__ counter,
+                                                     uint32_t P1x2, uint32_t K21x2) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned int t = 0;
+    if (lane == 0) t = atomicAdd(counter, 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if ((int)t >= ntasks) break;
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (seg[mid].first <= (int)t)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    const BatchSegment sg = seg[lo];
+    const BatchPair& p = pairs[sg.pair];
+    const int dx = sg.dx, dy = sg.dy;
+    uint8_t* dst = p.vols + (size_t)sg.r * p.vol_bytes;
+    const int local = (int)t - sg.first;
+    switch (p.D) {
+      case 32: agg_warp<2>(p.cost, dst, p.W, p.H, p.D, dx, dy, P1x2, K21x2, local * 16, warp); break;
+      case 64: agg_warp<4>(p.cost, dst, p.W, p.H, p.D, dx, dy, P1x2, K21x2, local * 8, warp); break;
+      case 128: agg_warp<8>(p.cost, dst, p.W, p.H, p.D, dx, dy, P1x2, K21x2, local * 4, warp); break;
+      default: agg_warp<16>(p.cost, dst, p.W, p.H, p.D, dx, dy, P1x2, K21x2, local * 2, warp); break;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kWtaThreads) k_wta_b(const BatchPair* __restrict__ pairs,
+                                                       const int* __restrict__ starts, int npairs,
+                                                       int ndirs) {
+  const int i = find_pair(starts, npairs, blockIdx.x);
+  const BatchPair& p = pairs[i];
+  const int b = blockIdx.x - starts[i];
+  const int P = kWtaThreads / (p.D >> 4);
+  const int nbx = (p.W + P - 1) / P;
+  wta_block(p.vols, ndirs, p.vol_bytes, nullptr, p.W, p.D, p.d_int, p.dsub, p.rkeys, b % nbx,
+            b / nbx);
+}
+
+__global__ void k_lr_b(const BatchPair* __restrict__ pairs, const int* __restrict__ starts,
+                       int npairs, int lr_tol) {
+  const int i = find_pair(starts, npairs, blockIdx.x);
+  const BatchPair& p = pairs[i];
+  const int b = blockIdx.x - starts[i];
+  const int nbx = (p.W + 255) / 256;
+  lr_block(p.d_int, p.dsub, p.rkeys, p.kappa, p.W, p.D, lr_tol, p.D1, b % nbx, b / nbx);
+}
+
+}  // namespace
+
+// Per-pair block counts of each stage (the host builds the prefix tables from these).
+void batch_stage_blocks(int W, int H, int D, int counts[kBatchStages]) {
+  counts[kStageKappa] = (H + 3) / 4;
+  counts[kStageCensus] = ((W + kCT_W - 1) / kCT_W) * ((H + kCT_H - 1) / kCT_H);
+  const int Pc = kCostThreads / (D / 16);
+  counts[kStageCost] = ((W + Pc - 1) / Pc) * H;
+  const size_t N = (size_t)W * H;
+  counts[kStageFill] = (int)((N + 4095) / 4096);
+  const int Pw = kWtaThreads / (D / 16);
+  counts[kStageWta] = ((W + Pw - 1) / Pw) * H;
+  counts[kStageLr] = ((W + 255) / 256) * H;
+}
+
+int batch_lines_per_warp(int D) { return 32 / (D / 16); }
+
+size_t batch_agg_smem(int warps_per_block) {
+  return (size_t)warps_per_block * kStages * 32 * sizeof(uint4);
+}
+
+void launch_batch_wave(cudaStream_t s, const BatchWaveDev& w, int P1, int P2, int lr_tol,
+                       int paths, int agg_warps, int agg_blocks) {
+  const uint32_t P1x2 = (uint32_t)P1 * 0x10001u, K21x2 = (uint32_t)(P2 - P1) * 0x10001u;
+  const int n = w.npairs;
+  k_kappa_b<<<w.total[kStageKappa], 128, 0, s>>>(w.pairs, w.starts[kStageKappa], n);
+  k_fill_b<<<w.total[kStageFill], 1024, 0, s>>>(w.pairs, w.starts[kStageFill], n);
+  k_census_b<<<2 * w.total[kStageCensus], dim3(kCT_W, kCT_H), 0, s>>>(w.pairs,
+                                                                     w.starts[kStageCensus], n,
+                                                                     w.total[kStageCensus]);
+  k_cost_b<<<w.total[kStageCost], kCostThreads, 0, s>>>(w.pairs, w.starts[kStageCost], n);
+  cudaMemsetAsync(w.counter, 0, sizeof(unsigned int), s);
+  const size_t smem = batch_agg_smem(agg_warps);
+  static size_t smem_set = 0;
+  if (smem > smem_set) {
+    cudaFuncSetAttribute(k_aggregate_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    smem_set = smem;
+  }
+  k_aggregate_b<<<agg_blocks, agg_warps * 32, smem, s>>>(w.pairs, w.segs, w.nseg, w.ntasks,
+                                                         w.counter, P1x2, K21x2);
+  k_wta_b<<<w.total[kStageWta], kWtaThreads, 4096 * sizeof(uint16_t), s>>>(
+      w.pairs, w.starts[kStageWta], n, paths);
+  k_lr_b<<<w.total[kStageLr], 256, 0, s>>>(w.pairs, w.starts[kStageLr], n, lr_tol);
+}
+
+void launch_batch_aggregate_only(cudaStream_t s, const BatchWaveDev& w, int P1, int P2,
+                                 int agg_warps, int agg_blocks) {
+  const uint32_t P1x2 = (uint32_t)P1 * 0x10001u, K21x2 = (uint32_t)(P2 - P1) * 0x10001u;
+  cudaMemsetAsync(w.counter, 0, sizeof(unsigned int), s);
+  const size_t smem = batch_agg_smem(agg_warps);
+  cudaFuncSetAttribute(k_aggregate_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_aggregate_b<<<agg_blocks, agg_warps * 32, smem, s>>>(w.pairs, w.segs, w.nseg, w.ntasks,
+                                                         w.counter, P1x2, K21x2);
+}
+
+int batch_max_blocks_per_sm(int agg_warps) {
+  cudaFuncSetAttribute(k_aggregate_b, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)batch_agg_smem(agg_warps));
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_aggregate_b, agg_warps * 32,
+                                                batch_agg_smem(agg_warps));
+  return n;
+}
+
+}  // namespace pd

@@ -22,6 +22,16 @@ struct pd_ctx {
   void* ws = nullptr;  // device scratch owned by the context
   size_t ws_bytes = 0;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  // batched path
+  size_t batch_budget = (size_t)32 << 30;
+  bool batch_graph = false, batch_autotune = true;
+  void* pinned = nullptr;  // host staging of the batch tables (page-locked)
+  size_t pinned_bytes = 0;
+  cudaEvent_t batch_done = nullptr;
+  bool batch_inflight = false;
+  cudaGraphExec_t graph_exec = nullptr;
+  void* graph_sig = nullptr;  // std::vector<long long>* signature of the captured batch
+  void* tuned = nullptr;      // std::map<signature, warps per block>*
   bool prof = false;
   pd_prof_rec* recs = nullptr;  // kMaxProf records, events created on first use
   int nrec = 0;

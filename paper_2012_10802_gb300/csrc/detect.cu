@@ -1,7 +1,7 @@
 // Sec. II-D and II-E on the GPU: SLIC superpixels on the transformed disparity map, the
 // superpixel-clustered map D3, the adaptive threshold of Eqs. (14)-(17) and the pothole mask.
 //
-// SLIC assignment is pixel-parallel: each 16x16 tile first gathers, in index order, the centres
+// SLIC assignment is pixel-parallel: each 32x32 tile first gathers, in index order, the centres
 // whose 2S x 2S search window can reach it, then every pixel scans that short list with the exact
 // window test, so the result equals the centre-by-centre sweep of the original algorithm (the
 // lower index wins ties).  Centre updates use exact integer sums (privatised per tile in shared
@@ -14,8 +14,9 @@ namespace pd {
 
 namespace {
 
-constexpr int kTile = 16;
-constexpr int kTileThreads = kTile * kTile;
+constexpr int kTile = 32;                         // SLIC assignment tile (pixels per side)
+constexpr int kTileThreads = 256;
+constexpr int kRowsPerPass = kTileThreads / 32;  // rows of the tile one pass of the block covers
 constexpr int kCandCap = 256;
 
 __device__ __forceinline__ int clampi(int x, int lo, int hi) { return x < lo ? lo : (x > hi ? hi : x); }
@@ -90,7 +91,8 @@ __global__ void k_slic_init_labels(int W, int H, int nx, int ny, int32_t* __rest
 }
 
 // One assignment round (if do_assign) plus the per-centre sums of the resulting labels:
-// acc[4k + 0..3] = members, sum x, sum y, sum rint(1024 D2).
+// acc[4k + 0..3] = members, sum x, sum y, sum rint(1024 D2).  A block covers a kTile x kTile tile;
+// thread (tx, ty) handles pixels (x0 + tx, y0 + ty + kRowsPerPass * i), so a warp is one row of 32.
 __global__ void __launch_bounds__(kTileThreads) k_slic_assign(
     const float* __restrict__ D2, int W, int H, int n, const float* __restrict__ cx,
     const float* __restrict__ cy, const float* __restrict__ cv, float Sf, float coef,
@@ -108,7 +110,7 @@ __global__ void __launch_bounds__(kTileThreads) k_slic_assign(
     // conservative box test (1 px margin); the exact test runs per pixel below
     const float bx0 = (float)x0 - 1.0f, bx1 = (float)(x0 + kTile), by0 = (float)y0 - 1.0f,
                 by1 = (float)(y0 + kTile);
-    constexpr int kBatch = 8;  // centres per thread loaded together before the ordered scan
+    constexpr int kBatch = 4;  // centres per thread loaded together before the ordered scan
     for (int base0 = 0; base0 < n; base0 += kBatch * kTileThreads) {
       float bx[kBatch], byy[kBatch];
 #pragma unroll
@@ -119,31 +121,31 @@ __global__ void __launch_bounds__(kTileThreads) k_slic_assign(
       }
 #pragma unroll
       for (int b = 0; b < kBatch; ++b) {
-      const int base = base0 + b * kTileThreads;
-      if (base >= n) break;  // block-uniform
-      int k = base + tid;
-      bool q = false;
-      float fx = bx[b], fy = byy[b];
-      if (k < n) q = (fx + Sf >= bx0) && (fx - Sf <= bx1) && (fy + Sf >= by0) && (fy - Sf <= by1);
-      unsigned bal = __ballot_sync(0xffffffffu, q);
-      if (lane == 0) wcount[warp] = __popc(bal);
-      __syncthreads();
-      int off = ncand;
-      for (int w = 0; w < warp; ++w) off += wcount[w];
-      int pos = off + __popc(bal & ((1u << lane) - 1u));
-      if (q && pos < kCandCap) {
-        cand[pos] = k;
-        ccx[pos] = fx;
-        ccy[pos] = fy;
-        ccv[pos] = cv[k];
-      }
-      __syncthreads();
-      if (tid == 0) {
-        int tot = ncand;
-        for (int w = 0; w < kTileThreads / 32; ++w) tot += wcount[w];
-        ncand = tot;
-      }
-      __syncthreads();
+        const int base = base0 + b * kTileThreads;
+        if (base >= n) break;  // block-uniform
+        const int k = base + tid;
+        const float fx = bx[b], fy = byy[b];
+        const bool q =
+            k < n && (fx + Sf >= bx0) && (fx - Sf <= bx1) && (fy + Sf >= by0) && (fy - Sf <= by1);
+        const unsigned bal = __ballot_sync(0xffffffffu, q);
+        if (lane == 0) wcount[warp] = __popc(bal);
+        __syncthreads();
+        int off = ncand;
+        for (int w = 0; w < warp; ++w) off += wcount[w];
+        const int pos = off + __popc(bal & ((1u << lane) - 1u));
+        if (q && pos < kCandCap) {
+          cand[pos] = k;
+          ccx[pos] = fx;
+          ccy[pos] = fy;
+          ccv[pos] = cv[k];
+        }
+        __syncthreads();
+        if (tid == 0) {
+          int tot = ncand;
+          for (int w = 0; w < kTileThreads / 32; ++w) tot += wcount[w];
+          ncand = tot;
+        }
+        __syncthreads();
       }
     }
   }
@@ -153,51 +155,54 @@ __global__ void __launch_bounds__(kTileThreads) k_slic_assign(
     sacc[i][0] = sacc[i][1] = sacc[i][2] = sacc[i][3] = 0ULL;
   __syncthreads();
 
-  const int x = x0 + (tid % kTile), y = y0 + (tid / kTile);
-  const bool inside = x < W && y < H;
-  int lab = -1, slot = -1;
-  long long q = 0;
-  if (inside) {
-    const size_t p = (size_t)y * W + x;
-    const float val = D2[p];
-    lab = labels[p];
-    if (do_assign) {
-      float best = INFINITY;
-      const float fxp = (float)x, fyp = (float)y;
-      if (!overflow) {
-        for (int i = 0; i < nc; ++i) {
-          float fx = fxp - ccx[i];
-          float fy = fyp - ccy[i];
-          if (!(fabsf(fx) <= Sf && fabsf(fy) <= Sf)) continue;
-          float dv = val - ccv[i];
-          float dd = dv * dv + (fx * fx + fy * fy) * coef;
-          if (dd < best) {
-            best = dd;
-            lab = cand[i];
-            slot = i;
+#pragma unroll
+  for (int pass = 0; pass < kTile / kRowsPerPass; ++pass) {
+    const int x = x0 + lane, y = y0 + warp + kRowsPerPass * pass;
+    const bool inside = x < W && y < H;
+    int lab = -1, slot = -1;
+    long long q = 0;
+    if (inside) {
+      const size_t p = (size_t)y * W + x;
+      const float val = D2[p];
+      lab = labels[p];
+      if (do_assign) {
+        float best = INFINITY;
+        const float fxp = (float)x, fyp = (float)y;
+        if (!overflow) {
+          for (int i = 0; i < nc; ++i) {
+            float fx = fxp - ccx[i];
+            float fy = fyp - ccy[i];
+            if (!(fabsf(fx) <= Sf && fabsf(fy) <= Sf)) continue;
+            float dv = val - ccv[i];
+            float dd = dv * dv + (fx * fx + fy * fy) * coef;
+            if (dd < best) {
+              best = dd;
+              lab = cand[i];
+              slot = i;
+            }
+          }
+        } else {  // rare: too many candidates for shared memory; scan every centre
+          for (int k = 0; k < n; ++k) {
+            float fx = fxp - cx[k];
+            float fy = fyp - cy[k];
+            if (!(fabsf(fx) <= Sf && fabsf(fy) <= Sf)) continue;
+            float dv = val - cv[k];
+            float dd = dv * dv + (fx * fx + fy * fy) * coef;
+            if (dd < best) {
+              best = dd;
+              lab = k;
+            }
           }
         }
-      } else {  // rare: too many candidates for shared memory; scan every centre
-        for (int k = 0; k < n; ++k) {
-          float fx = fxp - cx[k];
-          float fy = fyp - cy[k];
-          if (!(fabsf(fx) <= Sf && fabsf(fy) <= Sf)) continue;
-          float dv = val - cv[k];
-          float dd = dv * dv + (fx * fx + fy * fy) * coef;
-          if (dd < best) {
-            best = dd;
-            lab = k;
-          }
-        }
+        labels[p] = lab;
       }
-      labels[p] = lab;
+      q = __float2ll_rn(val * 1024.0f);  // exact scaling; rounds half to even like rint
     }
-    q = __float2ll_rn(val * 1024.0f);  // exact scaling; rounds half to even like rint
+    // a label's slot is the same for every lane that has it, so grouping by label groups by
+    // slot; lanes that kept an uncovered pixel's old label (slot -1) go straight to the global sums
+    warp_accumulate(inside && slot >= 0, lab, slot, x, y, q, sacc, acc);
+    warp_accumulate(inside && slot < 0, lab, -1, x, y, q, sacc, acc);
   }
-  // a label's slot is the same for every lane that has it, so grouping by label groups by slot;
-  // lanes that kept an uncovered pixel's old label (slot -1) go straight to the global sums
-  warp_accumulate(inside && slot >= 0, lab, slot, x, y, q, sacc, acc);
-  warp_accumulate(inside && slot < 0, lab, -1, x, y, q, sacc, acc);
   __syncthreads();
   if (!overflow)
     for (int i = tid; i < nc; i += kTileThreads) {
@@ -244,34 +249,31 @@ __global__ void k_centres_out(int n, const float* __restrict__ cx, const float* 
 // ------------------------------------------------------------------- Eqs. (14)-(17)
 constexpr int kBins = 257;  // k = 0..255 plus an overflow bin for everything at or above 32 px
 
-// Histograms of kmax = max(floor(a / 128), floor(b / 1024)) and kmin (the same with min), each
-// with exact sums n, sum a, sum b, sum a^2 + b^2, over interior pixels with a valid 3x3 window;
-// a = rint(1024 D2(p)), b = sum of rint(1024 D2) over the 8 neighbours.  Region 1 of threshold
-// k/8 is {kmax < k}, region 2 is {kmin >= k}.
-__device__ __forceinline__ long long warp_sum_ll(long long v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
 // Adds (1, a, b, a^2 + b^2) of the lanes sharing a bin into the shared histogram h, one lane per
-// distinct bin.  All 32 lanes must call it.
+// distinct bin.  All 32 lanes must call it.  The sums use the single-instruction warp reduction on
+// 32-bit values; a and b (D2 below 2^16 px) fit, a^2 + b^2 is split into 16/16/32-bit parts.
 __device__ void warp_hist(bool valid, int bin, long long a, long long b,
                           unsigned long long (*h)[4]) {
   const int lane = threadIdx.x & 31;
   unsigned pending = __ballot_sync(0xffffffffu, valid);
+  const unsigned long long sq = (unsigned long long)(a * a + b * b);
   while (pending) {
     const int leader = __ffs(pending) - 1;
     const int bl = __shfl_sync(0xffffffffu, bin, leader);
     const bool mine = valid && bin == bl;
     const unsigned peers = __ballot_sync(0xffffffffu, mine);
-    const long long sa = warp_sum_ll(mine ? a : 0);
-    const long long sb = warp_sum_ll(mine ? b : 0);
-    const long long sq = warp_sum_ll(mine ? a * a + b * b : 0);
+    const int sa = __reduce_add_sync(0xffffffffu, mine ? (int)a : 0);
+    const int sb = __reduce_add_sync(0xffffffffu, mine ? (int)b : 0);
+    const unsigned s0 = __reduce_add_sync(0xffffffffu, mine ? (unsigned)(sq & 0xffffu) : 0u);
+    const unsigned s1 = __reduce_add_sync(0xffffffffu, mine ? (unsigned)((sq >> 16) & 0xffffu) : 0u);
+    const unsigned s2 = __reduce_add_sync(0xffffffffu, mine ? (unsigned)(sq >> 32) : 0u);
     if (lane == leader) {
+      const unsigned long long ssq = (unsigned long long)s0 + ((unsigned long long)s1 << 16) +
+                                     ((unsigned long long)s2 << 32);
       atomicAdd(&h[bl][0], (unsigned long long)__popc(peers));
-      atomicAdd(&h[bl][1], (unsigned long long)sa);
-      atomicAdd(&h[bl][2], (unsigned long long)sb);
-      atomicAdd(&h[bl][3], (unsigned long long)sq);
+      atomicAdd(&h[bl][1], (unsigned long long)(long long)sa);
+      atomicAdd(&h[bl][2], (unsigned long long)(long long)sb);
+      atomicAdd(&h[bl][3], ssq);
     }
     pending &= ~peers;
   }
@@ -322,32 +324,55 @@ __global__ void __launch_bounds__(256) k_thresh_hist(const float* __restrict__ D
 // block takes the smallest minimising k; t_s from mode.
 constexpr int kSolveThreads = 256;
 
+// Inclusive block scan (sum) of one 64-bit value per thread; 256 threads.
+__device__ long long block_scan_ll(long long v, long long* tmp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 1; o < 32; o <<= 1) {
+    long long n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  if (lane == 31) tmp[warp] = v;
+  __syncthreads();
+  long long off = 0;
+  for (int w = 0; w < warp; ++w) off += tmp[w];
+  __syncthreads();
+  return v + off;
+}
+
 __global__ void __launch_bounds__(kSolveThreads) k_thresh_solve(
     const unsigned long long* __restrict__ hist, float delta_pd, int mode,
     double* __restrict__ thr, double* __restrict__ E2) {
-  __shared__ unsigned long long sh[2][kBins][4];
+  __shared__ long long tmp[kSolveThreads / 32];
   __shared__ double sE[kSolveThreads];
   __shared__ int sK[kSolveThreads];
   __shared__ double sMean[kSolveThreads];
-  for (int i = threadIdx.x; i < 2 * kBins * 4; i += kSolveThreads) (&sh[0][0][0])[i] = hist[i];
-  __syncthreads();
   const int k = threadIdx.x;
+  const unsigned long long(*hmax)[4] = reinterpret_cast<const unsigned long long(*)[4]>(hist);
+  const unsigned long long(*hmin)[4] = reinterpret_cast<const unsigned long long(*)[4]>(hist + kBins * 4);
+  // region 1 at threshold k: kmax bins 0..k-1 (exclusive prefix sums of bins 0..255);
+  // region 2 at threshold k: kmin bins k..256 (total minus the exclusive prefix)
+  long long r1[4], r2[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    long long xm = (long long)hmax[k][q];
+    r1[q] = block_scan_ll(xm, tmp) - xm;
+    long long xn = (long long)hmin[k][q];
+    r2[q] = block_scan_ll(xn, tmp) - xn;  // exclusive prefix of kmin bins below k
+  }
+  // totals of the kmin histogram over all 257 bins
+  __shared__ long long tot[4];
+  if (k < 4) {
+    long long t = 0;
+    for (int j = 0; j < kBins; ++j) t += (long long)hmin[j][k];
+    tot[k] = t;
+  }
+  __syncthreads();
   double e = NAN, mean = 0.0;
-  if (k >= 1 && k < 256) {
-    long long n1 = 0, a1 = 0, b1 = 0, n2 = 0, a2 = 0, b2 = 0;
-    unsigned long long s1 = 0, s2 = 0;
-    for (int j = 0; j < k; ++j) {
-      n1 += (long long)sh[0][j][0];
-      a1 += (long long)sh[0][j][1];
-      b1 += (long long)sh[0][j][2];
-      s1 += sh[0][j][3];
-    }
-    for (int j = k; j < kBins; ++j) {
-      n2 += (long long)sh[1][j][0];
-      a2 += (long long)sh[1][j][1];
-      b2 += (long long)sh[1][j][2];
-      s2 += sh[1][j][3];
-    }
+  if (k >= 1) {
+    long long n1 = r1[0], a1 = r1[1], b1 = r1[2];
+    unsigned long long s1 = (unsigned long long)r1[3];
+    long long n2 = tot[0] - r2[0], a2 = tot[1] - r2[1], b2 = tot[2] - r2[2];
+    unsigned long long s2 = (unsigned long long)tot[3] - (unsigned long long)r2[3];
     if (n1 != 0 && n2 != 0) {
       double e1 = (double)s1 - ((double)a1 * (double)a1 + (double)b1 * (double)b1) / (double)n1;
       double e2 = (double)s2 - ((double)a2 * (double)a2 + (double)b2 * (double)b2) / (double)n2;
@@ -355,7 +380,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_thresh_solve(
       mean = ((double)a2 / (double)n2) / 1024.0;
     }
   }
-  if (E2 && k < 256) E2[k] = e;
+  if (E2) E2[k] = e;
   // block argmin over the non-NaN energies, smallest k on ties
   sE[k] = e;
   sK[k] = k;

@@ -231,15 +231,30 @@ struct RollBest {
   int pad;
 };
 
+// Converts the 22 sums (after the count) to doubles, one per lane of the calling warp; the caller
+// synchronises before reading M.
 __device__ void load_moments(const int64_t* __restrict__ sums, MomD& M) {
-  int k = 1;  // skip the count; m[0][0] is the same number
-  for (int i = 0; i <= 4; ++i)
-    for (int j = 0; i + j <= 4; ++j, ++k)
-      M.m[i][j] = i128_to_double((unsigned long long)sums[2 * k], (long long)sums[2 * k + 1]);
-  for (int i = 0; i <= 2; ++i)
-    for (int j = 0; i + j <= 2; ++j, ++k)
-      M.q[i][j] = i128_to_double((unsigned long long)sums[2 * k], (long long)sums[2 * k + 1]);
-  M.qq = i128_to_double((unsigned long long)sums[2 * k], (long long)sums[2 * k + 1]);
+  const int t = threadIdx.x;
+  if (t >= 22) return;
+  const int k = t + 1;  // skip the count; m[0][0] is the same number
+  const double x = i128_to_double((unsigned long long)sums[2 * k], (long long)sums[2 * k + 1]);
+  if (t < 15) {  // m[i][j], i + j <= 4, i outer
+    int i = 0, r = t;
+    while (r >= 5 - i) {
+      r -= 5 - i;
+      ++i;
+    }
+    M.m[i][r] = x;
+  } else if (t < 21) {  // q[i][j], i + j <= 2
+    int i = 0, r = t - 15;
+    while (r >= 3 - i) {
+      r -= 3 - i;
+      ++i;
+    }
+    M.q[i][r] = x;
+  } else {
+    M.qq = x;
+  }
 }
 
 __device__ double coord_scale_d(int W, int H) {
@@ -309,7 +324,7 @@ __global__ void __launch_bounds__(kRollWarp) k_roll_grid(const int64_t* __restri
                                                          int order, int W, int H,
                                                          RollBest* __restrict__ res) {
   __shared__ MomD M;
-  if (threadIdx.x == 0) load_moments(sums, M);
+  load_moments(sums, M);
   __syncthreads();
   int k = blockIdx.x * kRollWarp + threadIdx.x;
   double e = INFINITY, beta[3];
@@ -328,7 +343,7 @@ __global__ void __launch_bounds__(kRollWarp) k_roll_round(const int64_t* __restr
                                                           int order, int W, int H, int round,
                                                           RollBest* __restrict__ res) {
   __shared__ MomD M;
-  if (threadIdx.x == 0) load_moments(sums, M);
+  load_moments(sums, M);
   __syncthreads();
   __shared__ double sa, ca;
   double a, b, phi;
@@ -358,7 +373,7 @@ __global__ void __launch_bounds__(kRollWarp) k_roll_final(const int64_t* __restr
                                                           pd_road_model* fitted,
                                                           RoadCoefF* coef) {
   __shared__ MomD M;
-  if (threadIdx.x == 0) load_moments(sums, M);
+  load_moments(sums, M);
   __syncthreads();
   const double sc = coord_scale_d(W, H);
   double phi = 0.0;

@@ -1,0 +1,427 @@
+// Device-side bodies of the Sec. II-A / II-B kernels, shared by the single-pair kernels (sgm.cu) and
+// the batched ones (batch.cu).  Each body takes its block coordinates explicitly.
+#pragma once
+
+#include "common.cuh"
+
+namespace pd {
+namespace body {
+
+constexpr uint32_t kFull = 0xffffffffu;
+constexpr uint32_t kBig2 = 0x3fff3fffu;  // "no neighbour": never the minimum, no u16 overflow
+
+__device__ __forceinline__ int clampi(int x, int lo, int hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+// ----------------------------------------------------------------------------- Eq. (6)
+// One warp per row: minimum of f(x, v) - delta_pt over x = 0..W-1, each f evaluated in double in
+// the fixed operation order of the model definition (the library is built without FMA
+// contraction).  f is monotone in x for the linear model and convex or concave in x for the
+// quadratic one, so the minimum over all x lies at an end point or, for a convex quadratic, next
+// to the vertex: the warp evaluates both end points and the 64 columns around the vertex.
+__device__ __forceinline__ double road_minus(double t1, double uc, double vc, double sn, int order,
+                                             double a0, double a1, double a2, double delta_pt,
+                                             int x) {
+  double t2 = ((double)x - uc) * sn;
+  double vp = (t1 - t2) + vc;
+  double f = a0 + a1 * vp;
+  if (order == 2) f = f + a2 * (vp * vp);
+  return f - delta_pt;
+}
+
+// Row v of Eq. (6), computed by one warp (lane = the calling lane).
+__device__ __forceinline__ void kappa_row(int W, int H, int order, double a0, double a1, double a2,
+                                          double cs, double sn, double delta_pt,
+                                          int32_t* __restrict__ kappa, int v, int lane) {
+  double uc = (double)(W - 1) * 0.5, vc = (double)(H - 1) * 0.5;
+  double t1 = ((double)v - vc) * cs;
+  double best = 1e300;
+  if (lane < 2) best = road_minus(t1, uc, vc, sn, order, a0, a1, a2, delta_pt, lane == 0 ? 0 : W - 1);
+  if (order == 2 && a2 > 0.0 && sn != 0.0) {
+    double xs = uc + ((t1 + vc) + a1 / (2.0 * a2)) / sn;  // column of the vertex vp = -a1 / (2 a2)
+    if (xs > -64.0 && xs < (double)W + 64.0) {
+      int xc = (int)floor(xs);
+      for (int x = xc - 31 + 2 * lane; x <= xc - 30 + 2 * lane; ++x)
+        if (x >= 0 && x < W) {
+          double f = road_minus(t1, uc, vc, sn, order, a0, a1, a2, delta_pt, x);
+          best = f < best ? f : best;
+        }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    double other = __shfl_xor_sync(kFull, best, o);
+    best = other < best ? other : best;
+  }
+  if (lane == 0) kappa[v] = (int32_t)floor(best);
+}
+
+// ----------------------------------------------------------------------------- census
+constexpr int kCT_W = 32, kCT_H = 8;
+
+// Census codes of one kCT_W x kCT_H tile (block of kCT_W x kCT_H threads), tile (bx, by).
+__device__ __forceinline__ void census_tile(const uint8_t* __restrict__ img, int W, int H,
+                                            size_t pitch, const int32_t* __restrict__ kappa,
+                                            uint32_t* __restrict__ codes, int bx, int by) {
+  __shared__ uint8_t tile[kCT_H + 4][kCT_W + 4];
+  int u0 = bx * kCT_W, v0 = by * kCT_H;
+  for (int i = threadIdx.y * kCT_W + threadIdx.x; i < (kCT_H + 4) * (kCT_W + 4);
+       i += kCT_W * kCT_H) {
+    int ty = i / (kCT_W + 4), tx = i % (kCT_W + 4);
+    int y = clampi(v0 + ty - 2, 0, H - 1);
+    int x = clampi(u0 + tx - 2, 0, W - 1);
+    if (kappa) x = clampi(x - kappa[y], 0, W - 1);  // the row-shifted image at (x, y)
+    tile[ty][tx] = img[(size_t)y * pitch + x];
+  }
+  __syncthreads();
+  int u = u0 + threadIdx.x, v = v0 + threadIdx.y;
+  if (u >= W || v >= H) return;
+  uint8_t c = tile[threadIdx.y + 2][threadIdx.x + 2];
+  uint32_t code = 0;
+  int k = 0;
+#pragma unroll
+  for (int dy = 0; dy < 5; ++dy)
+#pragma unroll
+    for (int dx = 0; dx < 5; ++dx) {
+      if (dx == 2 && dy == 2) continue;
+      code |= (uint32_t)(tile[threadIdx.y + dy][threadIdx.x + dx] < c) << k;
+      ++k;
+    }
+  codes[(size_t)v * W + u] = code;
+}
+
+// ----------------------------------------------------------------------------- cost
+// Interleaved layout, D % 16 == 0: one thread per (pixel, 16-disparity group), 16 bytes out.
+constexpr int kCostThreads = 256;
+
+// Interleaved cost of P = kCostThreads / (D/16) pixels of row v starting at u0 = bx * P.
+__device__ __forceinline__ void cost_il_block(const uint32_t* __restrict__ cl,
+                                              const uint32_t* __restrict__ cr, int W, int D,
+                                              uint8_t* __restrict__ cost, int bx, int v) {
+  __shared__ uint32_t sR[kCostThreads + kMaxD];
+  const int groups = D >> 4;
+  const int P = kCostThreads / groups;  // pixels per block
+  const int u0 = bx * P;
+  const int base = u0 - D + 1;
+  for (int i = threadIdx.x; i < P + D - 1; i += kCostThreads) {
+    int x = base + i;
+    sR[i] = (x >= 0 && x < W) ? cr[(size_t)v * W + x] : 0u;
+  }
+  __syncthreads();
+  const int u = u0 + threadIdx.x / groups;
+  const int g = threadIdx.x % groups;
+  if (u >= W) return;
+  const uint32_t c0 = cl[(size_t)v * W + u];
+  uint32_t w[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    uint32_t packed = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int p = 4 * i + b;
+      int d = 16 * g + (p >> 1) + ((p & 1) << 3);
+      int x = u - d;
+      uint32_t c = x >= 0 ? (uint32_t)__popc(c0 ^ sR[x - base]) : (uint32_t)kCensusBits;
+      packed |= c << (8 * b);
+    }
+    w[i] = packed;
+  }
+  *reinterpret_cast<uint4*>(cost + ((size_t)v * W + u) * D + 16 * g) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// ----------------------------------------------------------------------------- Eq. (8)
+constexpr int kAggWarps = 4;
+
+constexpr int kStages = 16;  // per-warp shared-memory ring of cost rows: kStages - 1 steps in flight
+
+// Asynchronous 16-byte copy global -> shared (cp.async, L2 only); src_bytes = 0 writes zeros and
+// reads nothing.
+__device__ __forceinline__ void cp_async16(uint32_t smem, const void* gmem, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem), "l"(gmem),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Every line of direction (dx, dy) is walked by a step index s; the pixel at step s moves by a
+// constant byte stride through the [H][W][D] volumes, and the line lies inside the image for one
+// contiguous range of s.  Horizontal lines are the rows (s runs along u); all other lines step
+// one row per s (s runs along v, in the direction of dy), and diagonal lines are indexed by
+// u - v (dx == dy) or u + v (dx == -dy).
+struct LineWalk {
+  long long off0;   // byte offset of step 0 (may lie outside the image)
+  long long delta;  // byte stride per step
+  int s_first, s_last, nsteps;
+};
+
+__device__ __forceinline__ LineWalk line_walk(int dx, int dy, int W, int H, int D, int line,
+                                              int first, int last, bool valid) {
+  LineWalk w;
+  if (dy == 0) {  // row `line`, s along u
+    const int u0 = dx > 0 ? 0 : W - 1;
+    w.off0 = ((long long)line * W + u0) * D;
+    w.delta = (long long)dx * D;
+    w.nsteps = W;
+    w.s_first = 0;
+    w.s_last = valid ? W - 1 : -1;
+    return w;
+  }
+  int vlo = 0, vhi = H - 1;
+  if (dx != 0) {  // the rows any line of this warp touches
+    if (dx == dy) {
+      vlo = max(0, H - 1 - last);
+      vhi = min(H - 1, W + H - 2 - first);
+    } else {
+      vlo = max(0, first - W + 1);
+      vhi = min(H - 1, last);
+    }
+  }
+  w.nsteps = vhi - vlo + 1;
+  const int v0 = dy > 0 ? vlo : vhi;
+  const int u0 = dx == 0 ? line : (dx == dy ? line - (H - 1) + v0 : line - v0);  // u at step 0
+  w.off0 = ((long long)v0 * W + u0) * D;
+  w.delta = ((long long)dy * W + dx) * D;
+  // steps with 0 <= u0 + s*dx <= W-1 and 0 <= s < nsteps
+  int lo = 0, hi = w.nsteps - 1;
+  if (dx > 0) {
+    lo = max(lo, -u0);
+    hi = min(hi, W - 1 - u0);
+  } else if (dx < 0) {
+    lo = max(lo, u0 - (W - 1));
+    hi = min(hi, u0);
+  }
+  w.s_first = lo;
+  w.s_last = valid ? hi : -1;
+  return w;
+}
+
+// The lines first .. first + 32/G - 1 of direction (dx, dy), walked by the calling warp (all 32
+// lanes call it; `warp` selects the warp's part of the block's cost ring).  L goes to dst_vol.
+template <int G>
+__device__ __forceinline__ void agg_warp(const uint8_t* __restrict__ cost,
+                                         uint8_t* __restrict__ dst_vol, int W, int H, int D,
+                                         int dx, int dy, uint32_t P1x2, uint32_t K21x2, int first,
+                                         int warp) {
+  constexpr int LPW = 32 / G;  // lines per warp
+  const int nlines = dy == 0 ? H : (dx == 0 ? W : W + H - 1);
+  const int lane = threadIdx.x & 31;
+  const int g = lane % G;
+  if (first >= nlines) return;  // the whole warp leaves together
+  const int line = first + lane / G;
+  const int last = min(first + LPW, nlines) - 1;
+  const LineWalk lw = line_walk(dx, dy, W, H, D, line, first, last, line < nlines);
+  const uint8_t* csrc = cost + 16 * g;
+  uint8_t* dst = dst_vol + 16 * g;
+
+  // State: L of the previous pixel on the line (the oracle's normalised value) and its minimum
+  // mp over all disparities, replicated in both u16 halves.  A line starts from L = 0, mp = 0,
+  // which makes its first pixel's L equal to the cost.
+  uint32_t N[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) N[j] = 0;
+  uint32_t mp = 0;
+
+  // Cost rows arrive through a per-warp ring in shared memory: stage k of lane `lane` holds the
+  // 16 cost bytes of one step.  Step s is read from stage s % kStages after waiting for its copy;
+  // the copy for step s + kStages - 1 then goes into the stage read one step earlier.
+  extern __shared__ uint4 s_ring[];
+  uint4* ring = s_ring + (size_t)warp * kStages * 32 + lane;
+  const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
+  long long pf_off = lw.off0;  // offset of the step being prefetched
+#pragma unroll
+  for (int k = 0; k < kStages - 1; ++k) {
+    const bool in = k >= lw.s_first && k <= lw.s_last;
+    cp_async16(ring_s + k * 32 * 16, csrc + (in ? pf_off : 0), in ? 16u : 0u);
+    cp_async_commit();
+    pf_off += lw.delta;
+  }
+  long long st_off = lw.off0;  // offset of the current step
+  for (int s0 = 0; s0 < lw.nsteps; s0 += kStages) {
+#pragma unroll
+    for (int k = 0; k < kStages; ++k) {
+      const int s = s0 + k;
+      if (s >= lw.nsteps) break;  // warp-uniform
+      const bool act = s >= lw.s_first && s <= lw.s_last;
+      cp_async_wait<kStages - 2>();  // the copy of step s is complete
+      const uint4 rv = ring[k * 32];
+      const uint32_t raw[4] = {rv.x, rv.y, rv.z, rv.w};
+      {
+        const int sp = s + kStages - 1;
+        const bool in = sp >= lw.s_first && sp <= lw.s_last;
+        cp_async16(ring_s + ((k + kStages - 1) % kStages) * 32 * 16, csrc + (in ? pf_off : 0),
+                   in ? 16u : 0u);
+        cp_async_commit();
+        pf_off += lw.delta;
+      }
+      // neighbours across the lane boundaries of this line's lane group
+      uint32_t prevHi = kBig2, nextLo = kBig2;
+      if constexpr (G > 1) {
+        uint32_t up = __shfl_up_sync(kFull, N[7], 1, G);
+        uint32_t dn = __shfl_down_sync(kFull, N[0], 1, G);
+        if (g > 0) prevHi = up;
+        if (g < G - 1) nextLo = dn;
+      }
+      const uint32_t left0 = __byte_perm(prevHi, N[7], 0x5432);
+      const uint32_t right7 = __byte_perm(N[0], nextLo, 0x5432);
+      const uint32_t K = mp + K21x2;  // m + P2 - P1 in both halves (no carry: all < 2^15)
+      uint32_t Lw[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        uint32_t lft = j == 0 ? left0 : N[j - 1];
+        uint32_t rgt = j == 7 ? right7 : N[j + 1];
+        // min(L[d-1], L[d+1], m + P2 - P1) + P1 against L[d]: the minimum of Eq. (8)
+        uint32_t t = __vimin3_u16x2(lft, rgt, K);
+        t = __viaddmin_u16x2(t, P1x2, N[j]);
+        uint32_t c = __byte_perm(raw[j >> 1], 0, (j & 1) ? 0x4342 : 0x4140);
+        // c + t - m in one 32-bit three-input add: each half of t is >= m, so no borrow or
+        // carry crosses between the halves
+        Lw[j] = t + c - mp;
+      }
+      uint32_t m = __vimin3_u16x2(__vimin3_u16x2(Lw[0], Lw[1], Lw[2]),
+                                  __vimin3_u16x2(Lw[3], Lw[4], Lw[5]), __vminu2(Lw[6], Lw[7]));
+      m = __vminu2(m, __byte_perm(m, m, 0x1032));  // both halves = min of the two halves
+#pragma unroll
+      for (int o = 1; o < G; o <<= 1) m = __vminu2(m, __shfl_xor_sync(kFull, m, o, G));
+      if (act) {
+        uint4 w;
+        w.x = __byte_perm(Lw[0], Lw[1], 0x6420);
+        w.y = __byte_perm(Lw[2], Lw[3], 0x6420);
+        w.z = __byte_perm(Lw[4], Lw[5], 0x6420);
+        w.w = __byte_perm(Lw[6], Lw[7], 0x6420);
+        __stcs(reinterpret_cast<uint4*>(dst + st_off), w);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) N[j] = Lw[j];
+        mp = m;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) N[j] = 0;
+        mp = 0;
+      }
+      st_off += lw.delta;
+    }
+  }
+  cp_async_wait<0>();  // no copy may still be in flight when the warp exits
+}
+
+// ------------------------------------------------------------- volume sums and Eq. (9)
+constexpr int kWtaThreads = 128;
+
+// Loads this thread's 16 disparities of S as planar u16x2 pairs (d = 16g + j, 16g + 8 + j).
+__device__ __forceinline__ void load_S_il(const uint8_t* __restrict__ vols, int ndirs,
+                                          size_t vol_bytes, size_t off, uint32_t sw[8]) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) sw[j] = 0;
+  for (int r = 0; r < ndirs; ++r) {
+    uint4 a = __ldcs(reinterpret_cast<const uint4*>(vols + (size_t)r * vol_bytes + off));
+    const uint32_t raw[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      sw[j] = __vadd2(sw[j], __byte_perm(raw[j >> 1], 0, (j & 1) ? 0x4342 : 0x4140));
+  }
+}
+
+__device__ __forceinline__ void load_S_nat(const uint16_t* __restrict__ S, size_t off,
+                                           uint32_t sw[8]) {
+  const uint4* src = reinterpret_cast<const uint4*>(S + off);
+  uint4 q0 = __ldg(src), q1 = __ldg(src + 1);
+  const uint32_t n[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};  // n[k]: d = 2k, 2k+1
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    sw[j] = __byte_perm(n[j >> 1], n[4 + (j >> 1)], (j & 1) ? 0x7632 : 0x5410);
+}
+
+// Natural-order u32 words k = 0..7 (d = 2k, 2k + 1) from planar pairs.
+__device__ __forceinline__ void planar_to_natural(const uint32_t sw[8], uint32_t o[8]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    o[k] = __byte_perm(sw[2 * k], sw[2 * k + 1], 0x5410);
+    o[4 + k] = __byte_perm(sw[2 * k], sw[2 * k + 1], 0x7632);
+  }
+}
+
+// One block covers P = 128 / G pixels of one row; G = D / 16 threads per pixel.
+// Writes d* (int16) and the sub-pixel value, and folds the right-view candidates of its pixels
+// into rkeys[v][x] = min over d of (S(x + d, d) << 8 | d) with one atomicMin per covered x.
+__device__ __forceinline__ void wta_block(const uint8_t* __restrict__ vols, int ndirs,
+                                          size_t vol_bytes, const uint16_t* __restrict__ S, int W,
+                                          int D, int16_t* __restrict__ d_int,
+                                          float* __restrict__ dsub, uint32_t* __restrict__ rkeys,
+                                          int bx, int v) {
+  extern __shared__ uint16_t sS[];  // [P][D]
+  const int G = D >> 4;
+  const int P = kWtaThreads / G;
+  const int u0 = bx * P;
+  const int Peff = min(P, W - u0);
+  const int pix = threadIdx.x / G, g = threadIdx.x % G;
+  const int u = u0 + pix;
+  uint32_t key = 0xffffffffu;
+  if (pix < Peff) {
+    size_t off = ((size_t)v * W + u) * D + 16 * g;
+    uint32_t sw[8], o[8];
+    if (S)
+      load_S_nat(S, off, sw);
+    else
+      load_S_il(vols, ndirs, vol_bytes, off, sw);
+    planar_to_natural(sw, o);
+    uint4* row = reinterpret_cast<uint4*>(sS + pix * D + 16 * g);
+    row[0] = make_uint4(o[0], o[1], o[2], o[3]);
+    row[1] = make_uint4(o[4], o[5], o[6], o[7]);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      uint32_t klo = ((sw[j] & 0xffffu) << 8) | (uint32_t)(16 * g + j);
+      uint32_t khi = ((sw[j] >> 16) << 8) | (uint32_t)(16 * g + 8 + j);
+      key = min(key, min(klo, khi));
+    }
+  }
+  for (int o = 1; o < G; o <<= 1) key = min(key, __shfl_xor_sync(kFull, key, o, G));
+  __syncthreads();
+  if (pix < Peff && g == 0) {
+    int ds = (int)(key & 0xffu);
+    float sub = (float)ds;
+    if (ds > 0 && ds < D - 1) {
+      int a = sS[pix * D + ds - 1], b = sS[pix * D + ds], c = sS[pix * D + ds + 1];
+      int num = a - c;
+      int den = 2 * (a + c - 2 * b);
+      if (den > 0) sub = (float)ds + (float)num / (float)den;
+    }
+    d_int[(size_t)v * W + u] = (int16_t)ds;
+    dsub[(size_t)v * W + u] = sub;
+  }
+  // right view: x in [u0 - D + 1, u0 + Peff - 1], candidates d with u0 <= x + d < u0 + Peff
+  for (int i = threadIdx.x; i < Peff + D - 1; i += kWtaThreads) {
+    int x = u0 - D + 1 + i;
+    if (x < 0) continue;
+    int dlo = max(0, u0 - x);
+    int dhi = min(D - 1, u0 + Peff - 1 - x);
+    uint32_t best = 0xffffffffu;
+    for (int d = dlo; d <= dhi; ++d) {
+      uint32_t k = ((uint32_t)sS[(x + d - u0) * D + d] << 8) | (uint32_t)d;
+      best = k < best ? k : best;
+    }
+    if (dlo <= dhi) atomicMin(rkeys + (size_t)v * W + x, best);
+  }
+}
+
+__device__ __forceinline__ void lr_block(const int16_t* __restrict__ d_int,
+                                         const float* __restrict__ dsub,
+                                         const uint32_t* __restrict__ rkeys,
+                                         const int32_t* __restrict__ kappa, int W, int D, int lr_tol,
+                                         float* __restrict__ D1, int bx, int v) {
+  int u = bx * blockDim.x + threadIdx.x;
+  if (u >= W) return;
+  size_t p = (size_t)v * W + u;
+  int ds = d_int[p];
+  int xr = u - ds;
+  bool valid = u >= D - 1 && xr >= 0;
+  if (valid) {
+    int dr = (int)(rkeys[(size_t)v * W + xr] & 0xffu);
+    valid = abs(ds - dr) <= lr_tol;
+  }
+  float d1 = dsub[p] + (float)kappa[v];
+  D1[p] = (valid && d1 >= 0.0f) ? d1 : -1.0f;
+}
+
+}  // namespace body
+}  // namespace pd
