@@ -66,6 +66,9 @@ def _declare(L):
         "or_superpixel_mean": (None, [_P, _P, _i, _i, _i, _P]),
         "or_threshold": (_i, [_P, _P, _i, _i, _f, _i, C.POINTER(_d), C.POINTER(_d), _P]),
         "or_mask": (None, [_P, _i, _i, _d, _P]),
+        "or_band_windows": (None, [_P, _i, _i, _i, _i, _P, _P]),
+        "or_aggregate_band": (None, [_P, _P, _P, _i, _i, _i, _i, _i, _i, _P]),
+        "or_disparity_band": (None, [_P, _P, _P, _i, _i, _i, _P, _i, _P, _P]),
         "or_moment_sums_size": (C.c_size_t, []),
         "or_moments_export": (None, [_P, _P]),
     }
@@ -304,3 +307,44 @@ def pipeline(left, right, model, p: Params, keep_volumes=False):
                 "D3": D3, "t_r": t_r, "t_s": t_s, "E2": E2,
                 "mask": mask(D3, t_s)})
     return out
+
+
+# ----------------------------------------------------------------------------- learned band
+
+def band_windows(tile_lo, W, H, D, band=17):
+    tl = _c(tile_lo, np.int16)
+    lo = np.empty((H, W), np.int16)
+    hi = np.empty((H, W), np.int16)
+    lib().or_band_windows(_ptr(tl), W, H, D, band, _ptr(lo), _ptr(hi))
+    return lo, hi
+
+
+def aggregate_band(cst, lo, hi, paths, P1, P2):
+    cst = _c(cst, np.uint8)
+    H, W, D = cst.shape
+    out = np.empty((H, W, D), np.uint16)
+    lib().or_aggregate_band(_ptr(cst), _ptr(_c(lo, np.int16)), _ptr(_c(hi, np.int16)), W, H, D,
+                            paths, P1, P2, _ptr(out))
+    return out
+
+
+def disparity_band(S, lo, hi, kap, lr_tol):
+    S = _c(S, np.uint16)
+    H, W, D = S.shape
+    d_int = np.empty((H, W), np.int16)
+    D1 = np.empty((H, W), np.float32)
+    lib().or_disparity_band(_ptr(S), _ptr(_c(lo, np.int16)), _ptr(_c(hi, np.int16)), W, H, D,
+                            _ptr(_c(kap, np.int32)), lr_tol, _ptr(d_int), _ptr(D1))
+    return d_int, D1
+
+
+def sgm_band(left, right, model, p: Params, tile_lo, band=17):
+    """Sec. II-A/II-B with the disparity search restricted to per-tile windows."""
+    H, W = left.shape
+    kap = kappa(model, W, H, p.delta_pt)
+    rw = warp(right, kap)
+    cst = cost(census(left), census(rw), p.D)
+    lo, hi = band_windows(tile_lo, W, H, p.D, band)
+    S = aggregate_band(cst, lo, hi, p.paths, p.P1, p.P2)
+    d_int, D1 = disparity_band(S, lo, hi, kap, p.lr_tol)
+    return {"kappa": kap, "lo": lo, "hi": hi, "S": S, "d_int": d_int, "D1": D1}

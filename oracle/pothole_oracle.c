@@ -18,7 +18,10 @@
  *   R6 road pixels = all left-right-consistent pixels, fixed-point moments;
  *   R7 roll: closed form for the linear model, grid + golden section for the quadratic one;
  *   R8 SLIC grid/tie rules, fixed iteration count;
- *   R9 threshold regions on the diagonal with exact (fixed-point) g; t_s from the road mean.
+ *   R9 threshold regions on the diagonal with exact (fixed-point) g; t_s from the road mean;
+ *   R10 (band SGM, beyond the paper) per-16x16-tile windows [lo, lo + band) clipped to [0, D),
+ *       L = +infinity outside the window, minima of Eq. (8) over the previous pixel's window,
+ *       winners and right views over in-window candidates, valid pixels need u >= hi - 1.
  */
 #include "pothole_oracle.h"
 
@@ -707,4 +710,124 @@ void or_moments_export(const or_moment_sums* mom, int64_t* out) {
     out[2 * i] = (int64_t)(uint64_t)vals[i];
     out[2 * i + 1] = (int64_t)(vals[i] >> 64);
   }
+}
+
+/* ------------------------------------------------ learned-band SGM (an extension of the paper) */
+
+/* Reading R10.  Each 16x16 tile (tile (u/16, v/16)) searches the window [lo, lo + band) clipped to
+ * [0, D), or the full range [0, D) when its entry of tile_lo is negative.  Writes each pixel's
+ * window as [lo[p], hi[p]). */
+void or_band_windows(const int16_t* tile_lo, int W, int H, int D, int band, int16_t* lo,
+                     int16_t* hi) {
+  int tw = (W + 15) / 16;
+  for (int v = 0; v < H; ++v)
+    for (int u = 0; u < W; ++u) {
+      int t = tile_lo[(v / 16) * tw + (u / 16)];
+      int a = 0, b = D;
+      if (t >= 0) {
+        a = clampi(t, 0, D - 1);
+        b = a + band < D ? a + band : D;
+      }
+      lo[(size_t)v * W + u] = (int16_t)a;
+      hi[(size_t)v * W + u] = (int16_t)b;
+    }
+}
+
+/* Eq. (8) restricted to the windows: L_r(p, d) exists for d in [lo(p), hi(p)); the terms of the
+ * minimum use only d' inside the predecessor's window, and m is the minimum over that window.
+ * S is 0xFFFF outside the window. */
+void or_aggregate_band(const uint8_t* cost, const int16_t* lo, const int16_t* hi, int W, int H,
+                       int D, int paths, int P1, int P2, uint16_t* S) {
+  const int64_t INF = (int64_t)1 << 40;
+  size_t n = (size_t)W * H * D;
+  int64_t* L = (int64_t*)malloc(sizeof(int64_t) * n);
+  int64_t* acc = (int64_t*)calloc(n, sizeof(int64_t));
+  for (int r = 0; r < paths; ++r) {
+    int dx = kDirs[r][0], dy = kDirs[r][1];
+    int v0, vi, u0, ui;
+    path_order(H, dy, &v0, &vi);
+    path_order(W, dx, &u0, &ui);
+    for (int iv = 0, v = v0; iv < H; ++iv, v += vi) {
+      for (int iu = 0, u = u0; iu < W; ++iu, u += ui) {
+        size_t p = (size_t)v * W + u;
+        const uint8_t* c = cost + p * D;
+        int64_t* out = L + p * D;
+        for (int d = 0; d < D; ++d) out[d] = INF;
+        int pu = u - dx, pv = v - dy;
+        if (pu < 0 || pu >= W || pv < 0 || pv >= H) {
+          for (int d = lo[p]; d < hi[p]; ++d) out[d] = c[d];
+          continue;
+        }
+        size_t q = (size_t)pv * W + pu;
+        const int64_t* prev = L + q * D;
+        int plo = lo[q], phi = hi[q];
+        int64_t m = INF;
+        for (int d = plo; d < phi; ++d)
+          if (prev[d] < m) m = prev[d];
+        for (int d = lo[p]; d < hi[p]; ++d) {
+          int64_t best = m + P2;
+          if (d >= plo && d < phi && prev[d] < best) best = prev[d];
+          if (d - 1 >= plo && d - 1 < phi && prev[d - 1] + P1 < best) best = prev[d - 1] + P1;
+          if (d + 1 >= plo && d + 1 < phi && prev[d + 1] + P1 < best) best = prev[d + 1] + P1;
+          out[d] = c[d] + best - m;
+        }
+      }
+    }
+    for (size_t i = 0; i < n; ++i)
+      if (L[i] < INF) acc[i] += L[i];
+  }
+  for (int v = 0; v < H; ++v)
+    for (int u = 0; u < W; ++u) {
+      size_t p = (size_t)v * W + u;
+      for (int d = 0; d < D; ++d)
+        S[p * D + d] = (d >= lo[p] && d < hi[p]) ? (uint16_t)acc[p * D + d] : (uint16_t)0xFFFF;
+    }
+  free(L);
+  free(acc);
+}
+
+/* Eqs. (9)-(10) over the windows: d* = argmin over [lo, hi); the parabola needs d* - 1 and
+ * d* + 1 inside the window; the right view of column x takes the d with x + d inside the image
+ * and d inside the window of pixel x + d; valid pixels need u >= hi - 1, a right view at u - d*
+ * and |d* - d_R| <= lr_tol. */
+void or_disparity_band(const uint16_t* S, const int16_t* lo, const int16_t* hi, int W, int H, int D,
+                       const int32_t* kappa, int lr_tol, int16_t* d_int, float* D1) {
+  int* dright = (int*)malloc(sizeof(int) * (size_t)W);
+  for (int v = 0; v < H; ++v) {
+    const uint16_t* row = S + (size_t)v * W * D;
+    for (int x = 0; x < W; ++x) {
+      int best = -1;
+      unsigned bestv = 0;
+      for (int d = 0; d < D && x + d < W; ++d) {
+        size_t p = (size_t)v * W + x + d;
+        if (d < lo[p] || d >= hi[p]) continue;
+        unsigned val = row[(size_t)(x + d) * D + d];
+        if (best < 0 || val < bestv) {
+          bestv = val;
+          best = d;
+        }
+      }
+      dright[x] = best;
+    }
+    for (int u = 0; u < W; ++u) {
+      size_t p = (size_t)v * W + u;
+      const uint16_t* s = row + (size_t)u * D;
+      int a = lo[p], b = hi[p];
+      int ds = a;
+      for (int d = a + 1; d < b; ++d)
+        if (s[d] < s[ds]) ds = d;
+      float dsub = (float)ds;
+      if (ds - 1 >= a && ds + 1 < b) {
+        int num = (int)s[ds - 1] - (int)s[ds + 1];
+        int den = 2 * ((int)s[ds - 1] + (int)s[ds + 1] - 2 * (int)s[ds]);
+        if (den > 0) dsub = (float)ds + (float)num / (float)den;
+      }
+      d_int[p] = (int16_t)ds;
+      int xr = u - ds;
+      int valid = u >= b - 1 && xr >= 0 && dright[xr] >= 0 && abs(ds - dright[xr]) <= lr_tol;
+      float d1 = dsub + (float)kappa[v];
+      D1[p] = (valid && d1 >= 0.0f) ? d1 : -1.0f;
+    }
+  }
+  free(dright);
 }

@@ -96,6 +96,15 @@ int or_threshold(const float* D2, const float* D1, int W, int H, float delta_pd,
 /* Sec. II-E: pothole mask = D3 < t_s. */
 void or_mask(const float* D3, int W, int H, double t_s, uint8_t* mask);
 
+/* Learned-band SGM (an extension beyond the paper): per-tile windows, aggregation restricted to
+ * the windows (S = 0xFFFF outside), and the disparity step over the windows. */
+void or_band_windows(const int16_t* tile_lo, int W, int H, int D, int band, int16_t* lo,
+                     int16_t* hi);
+void or_aggregate_band(const uint8_t* cost, const int16_t* lo, const int16_t* hi, int W, int H,
+                       int D, int paths, int P1, int P2, uint16_t* S);
+void or_disparity_band(const uint16_t* S, const int16_t* lo, const int16_t* hi, int W, int H, int D,
+                       const int32_t* kappa, int lr_tol, int16_t* d_int, float* D1);
+
 /* Test-harness helpers: the size of or_moment_sums, and its 23 sums as (low, high) 64-bit pairs. */
 size_t or_moment_sums_size(void);
 void or_moments_export(const or_moment_sums* mom, int64_t* out);
