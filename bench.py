@@ -19,6 +19,7 @@ import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+HERE = ROOT
 sys.path.insert(0, ROOT)
 
 W_, H_, D_, PATHS_ = 1280, 720, 128, 8
@@ -41,6 +42,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-pair mixed batch")
+    ap.add_argument("--no-band", action="store_true", help="skip the learned-band comparison")
     ap.add_argument("--size", default=None,
                     help="WxH of a smaller road for profiling captures (not a benchmark line)")
     return ap.parse_args()
@@ -111,13 +113,22 @@ def measured_peaks():
         return {}
 
 
+AGG_SOURCES = ("sgm.cu", "sgm_body.cuh", "common.cuh")
+
+
+def agg_source_sha256():
+    h = hashlib.sha256()
+    for f in AGG_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2012_10802_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def agg_traffic_record():
     """DRAM bytes per launch of the aggregation kernel from the committed ncu summary, if the
-    kernel source is unchanged since the counters were taken."""
+    kernel's sources are unchanged since the counters were taken."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "aggregate_traffic.json")))
-        src = open(os.path.join(ROOT, "paper_2012_10802_gb300", "csrc", "sgm.cu"), "rb").read()
-        if rec.get("sgm_cu_sha256") == hashlib.sha256(src).hexdigest():
+        if rec.get("source_sha256") == agg_source_sha256():
             return rec.get("dram_bytes_per_launch_full")
     except (OSError, ValueError):
         pass
@@ -222,6 +233,78 @@ def bench_batch(B, torch, synth, n_pairs=64, steps=5, seq_steps=2):
             "sequential_ms": ts, "sequential_frames_per_s": n_pairs / (ts * 1e-3),
             "sequential_Mdisp_s": disp / (ts * 1e-3) / 1e6, "speedup": ts / tb,
             "identical_to_sequential": bool(same)}
+
+
+def bench_band(B, torch, synth, steps=10, n_eval=4):
+    """The learned band at 1920x1080, D = 128, 8 paths: the band network (committed weights,
+    trained on 2000 synthetic pairs by the library's own kernels) picks a 17-disparity window per
+    16x16 tile, against the full-range SGM on the same pairs.  Times are CUDA-event medians on the
+    library stream with L2 flushed before each call; disagreement is the fraction of pixels with
+    u >= D - 1 whose validity or (valid) integer disparity differs from the full range."""
+    from paper_2012_10802_gb300 import band
+    W, H, D = 1920, 1080, 128
+    if not os.path.exists(band.WEIGHTS):
+        return {"unavailable": "no trained weights at " + os.path.relpath(band.WEIGHTS, HERE)}
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(stream):
+        ctx = B.Context(torch.cuda.current_device(), stream=stream)
+        net = B.Cnn(torch.cuda.current_device(), 1, (H + 3) // 4, (W + 3) // 4)
+        B.pd_cnn_set_params(ctx, net, band.load_params())
+        p = B.default_params(D=D)
+        dis, frac, const_dis, pairs = [], [], [], []
+        for i in range(n_eval):
+            sc = synth.road_scaled(W, H, band.TEST_SEED0 + i)
+            left, right = synth.render_torch(sc, "cuda")
+            model = B.RoadModel.make(*synth.true_model(sc))
+            pairs.append((left, right, model))
+            kap, d_full, D1_full = B.pd_sgm(ctx, left, right, model, p)
+            tl, _, d, D1 = B.pd_sgm_learned(ctx, net, left, right, model, p, 17)
+            dis.append(band.disagreement(d, D1, d_full, D1_full, D))
+            frac.append((tl >= 0).float().mean().item())
+            c0 = int(d_full[D1_full >= 0].float().median().item())
+            tl_c = torch.full_like(tl, max(0, min(c0 - 8, D - 17)))
+            _, d_c, D1_c = B.pd_sgm_band(ctx, left, right, model, p, tl_c, 17)
+            const_dis.append(band.disagreement(d_c, D1_c, d_full, D1_full, D))
+
+        def timed(fn):
+            for _ in range(3):
+                fn()
+            ms = []
+            for _ in range(steps):
+                flush.fill_(3)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            return statistics.median(ms)
+
+        left, right, model = pairs[0]
+        kap, d_int, D1 = B.pd_sgm(ctx, left, right, model, p)
+        tl = ctx.empty(((H + 15) // 16, (W + 15) // 16), torch.int16)
+        x = B.pd_band_input(ctx, left, right, kap)
+        out = B.pd_cnn_forward(ctx, net, x)
+        full_ms = timed(lambda: B.pd_sgm(ctx, left, right, model, p, kap, d_int, D1))
+        learned_ms = timed(lambda: B.pd_sgm_learned(ctx, net, left, right, model, p, 17, tl, kap,
+                                                    d_int, D1))
+        cnn_ms = timed(lambda: (B.pd_band_input(ctx, left, right, kap, x),
+                                B.pd_cnn_forward(ctx, net, x, out)))
+        band_only_ms = timed(lambda: B.pd_sgm_band(ctx, left, right, model, p, tl, 17, kap, d_int,
+                                                   D1))
+        net.close()
+        ctx.close()
+    disp = W * H * D
+    return {"workload": "road_1920x1080_d128_8paths, learned 17-disparity band per 16x16 tile "
+                        "(conf >= 0.9) vs full range; %d test pairs" % n_eval,
+            "full_range_ms": full_ms, "learned_ms": learned_ms, "speedup": full_ms / learned_ms,
+            "learned_Mdisp_s": disp / (learned_ms * 1e-3) / 1e6,
+            "full_range_Mdisp_s": disp / (full_ms * 1e-3) / 1e6,
+            "cnn_ms": cnn_ms, "band_sgm_ms": band_only_ms,
+            "banded_tile_fraction": statistics.mean(frac),
+            "disagreement_mean": statistics.mean(dis), "disagreement_max": max(dis),
+            "constant_centre_disagreement_mean": statistics.mean(const_dis)}
 
 
 def main():
@@ -357,6 +440,9 @@ def main():
     batch = None
     if not args.no_batch and not args.size:
         batch = bench_batch(B, torch, synth)
+    band_res = None
+    if not args.no_band and not args.size:
+        band_res = bench_band(B, torch, synth)
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -379,7 +465,7 @@ def main():
                    "stage_ms": {k: prof[k] / calls for k in ("prep_ms", "aggregate_ms",
                                                             "disparity_ms", "transform_ms",
                                                             "superpixel_ms", "mask_ms")},
-                   "wall_s": wall, "batch64": batch},
+                   "wall_s": wall, "batch64": batch, "band1080": band_res},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": prof["launches"], "clocks": clocks,
     }

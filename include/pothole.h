@@ -288,6 +288,88 @@ pd_status pd_batch_config(pd_ctx* ctx, size_t scratch_budget_bytes, int use_grap
  * context to pass its table upload before reusing the host staging buffer. */
 pd_status pd_sgm_batch(pd_ctx* ctx, const pd_pair* pairs, int n, const pd_params* params);
 
+/* -------------------------------------- learned disparity band (an extension of the paper) */
+
+/* Sec. II-A and II-B with the disparity search of each 16x16 tile restricted to a window:
+ * tile (tx, ty) = (u / 16, v / 16) searches [lo, min(lo + band_width, D)) with
+ * lo = min(tile_lo[ty][tx], D - 1), or the full range [0, D) where tile_lo[ty][tx] < 0.  Eq. (8)
+ * runs over the windows with L = infinity outside them (its minima use only the previous pixel's
+ * window); d* is the argmin over the window (smallest d on ties); the parabola needs d* - 1 and
+ * d* + 1 inside the window; the right view of column x takes the candidates d inside the window
+ * of pixel x + d; a pixel is valid when u >= hi - 1, u - d* >= 0 and |d* - d_R(u - d*)| <=
+ * lr_tol.  With every tile_lo negative the results equal pd_sgm's.
+ * tile_lo: int16 [ceil(H/16)][ceil(W/16)] (device); band_width in 1..D; other arguments as in
+ * pd_sgm (D in {32, 64, 128, 256}). */
+pd_status pd_sgm_band(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H,
+                      size_t pitch, const pd_road_model* model, const pd_params* params,
+                      const int16_t* tile_lo, int band_width, int32_t* kappa, int16_t* d_int,
+                      float* D1);
+
+/* The band network: per 16x16 tile of the row-shifted pair, a disparity centre and a confidence
+ * (an extension beyond the paper; it restates no passage of it).  Input x: bf16 [B][Hd][Wd][2],
+ * Hd = ceil(H/4), Wd = ceil(W/4), as written by pd_band_input.  Four 3x3 convolutions with zero
+ * padding 1, strides 1, 2, 2, 1 and channels 2 -> 32 -> 32 -> 32 -> 2, ReLU after the first three;
+ * bf16 operands, fp32 accumulation, bf16 activations.  Output out: float [B][Ho][Wo][2] with
+ * Ho = ceil(Hd/4) = ceil(H/16) (likewise Wo): channel 0 = centre / 16 (pixels of the shifted
+ * pair), channel 1 = logit of the confidence that the tile's disparities lie within +-7 of it.
+ * Parameters: 19682 floats, per layer the weights [Cout][3][3][Cin] then the Cout biases. */
+typedef struct pd_cnn pd_cnn;
+
+/* Allocates a network (zero parameters) whose calls accept up to max_batch images of at most
+ * max_hd x max_wd input cells on `device`.  PD_ERR_OOM if the buffers do not fit. */
+pd_status pd_cnn_create(pd_cnn** net, int device, int max_batch, int max_hd, int max_wd);
+pd_status pd_cnn_destroy(pd_cnn* net);
+int pd_cnn_num_params(void);
+
+/* Copies n = pd_cnn_num_params() parameters from / to host memory (synchronous on ctx's stream);
+ * set_params also clears the Adam state and its step count. */
+pd_status pd_cnn_set_params(pd_ctx* ctx, pd_cnn* net, const float* host_params, int n);
+pd_status pd_cnn_get_params(pd_ctx* ctx, pd_cnn* net, float* host_params, int n);
+
+/* Forward pass; x and out are device pointers (layouts above). */
+pd_status pd_cnn_forward(pd_ctx* ctx, pd_cnn* net, const void* x, int B, int Hd, int Wd,
+                         float* out);
+
+/* Loss and its gradient with respect to the parameters.  targets: float [B][Ho][Wo][4] = (centre
+ * in pixels, confidence label 0/1, centre weight, confidence weight).  Loss = sum of centre
+ * weight * Huber_1(out0 - centre / 16) / max(1, total centre weight) + sum of confidence weight *
+ * logistic loss(out1, label) / max(1, total confidence weight).  loss: one float, grad: float
+ * [19682], both device. */
+pd_status pd_cnn_loss_grad(pd_ctx* ctx, pd_cnn* net, const void* x, const float* targets, int B,
+                           int Hd, int Wd, float* loss, float* grad);
+
+/* pd_cnn_loss_grad followed by one Adam step (beta 0.9 / 0.999, eps 1e-8) of size lr on the fp32
+ * master parameters.  loss (device, may be NULL) receives the loss before the step. */
+pd_status pd_cnn_train_step(pd_ctx* ctx, pd_cnn* net, const void* x, const float* targets, int B,
+                            int Hd, int Wd, float lr, float* loss);
+
+/* The network input of one pair: the right image shifted row by row as in Sec. II-A
+ * (right(clamp(u - kappa(v)))), both images summed over 4x4 blocks (edge rows and columns
+ * repeated), mapped to (sum - 2048) / 1024 and rounded to bf16.  x: bf16 [Hd][Wd][2] (device). */
+pd_status pd_band_input(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H,
+                        size_t pitch, const int32_t* kappa, void* x);
+
+/* Training targets from a full-range result: per 16x16 tile, with n valid pixels (D1 >= 0), the
+ * lower median c of their d*, confidence label 1 iff n >= 64 and at least 99.5 % lie in
+ * [c - 7, c + 7], centre weight 1 iff n >= 64, confidence weight 1.  targets: float
+ * [ceil(H/16)][ceil(W/16)][4] (device). */
+pd_status pd_band_labels(pd_ctx* ctx, const int16_t* d_int, const float* D1, int W, int H, int D,
+                         float* targets);
+
+/* Windows from the network output: tiles with out1 >= ln 9 (confidence >= 0.9) start at
+ * rint(16 out0) - band_width / 2 moved into [0, D - band_width]; the others get -1 (full range).
+ * cnn_out: float [tiles_h][tiles_w][2]; tile_lo: int16 [tiles_h][tiles_w] (device). */
+pd_status pd_band_tiles(pd_ctx* ctx, const float* cnn_out, int tiles_h, int tiles_w, int D,
+                        int band_width, int16_t* tile_lo);
+
+/* The learned band path of one pair: row shifts, pd_band_input, the network, pd_band_tiles and
+ * pd_sgm_band.  tile_lo (device, may be NULL) receives the windows used; the network must accept
+ * one image of ceil(H/4) x ceil(W/4). */
+pd_status pd_sgm_learned(pd_ctx* ctx, pd_cnn* net, const uint8_t* left, const uint8_t* right,
+                         int W, int H, size_t pitch, const pd_road_model* model,
+                         const pd_params* params, int band_width, int16_t* tile_lo,
+                         int32_t* kappa, int16_t* d_int, float* D1);
+
 /* -------------------------------------------------------------------------- whole path */
 
 /* pd_sgm, pd_transform, pd_superpixels and pd_pothole_mask in sequence on one stream.

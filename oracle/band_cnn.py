@@ -113,8 +113,14 @@ def conv3x3(x, w, b, stride):
     return y
 
 
-def forward(theta, x):
-    """Returns the output [B][Ho][Wo][2] and the per-layer inputs and pre-activations."""
+def _stored(a, bf16):
+    return bf16_round(a.astype(np.float32)).astype(np.float64) if bf16 else a
+
+
+def forward(theta, x, store_bf16=False):
+    """Returns the output [B][Ho][Wo][2] and the per-layer inputs and pre-activations.  With
+    store_bf16 the activations between layers are rounded to bfloat16, the storage format of the
+    GPU network (its arithmetic is otherwise the same sums)."""
     h = np.asarray(x, np.float64)
     if h.ndim == 3:
         h = h[None]
@@ -122,7 +128,7 @@ def forward(theta, x):
     for (w, b), (_, _, s, relu) in zip(unpack(np.asarray(theta, np.float64)), LAYERS):
         z = conv3x3(h, w, b, s)
         cache.append((h, z))
-        h = np.maximum(z, 0.0) if relu else z
+        h = _stored(np.maximum(z, 0.0), store_bf16) if relu else z
     return h, cache
 
 
@@ -149,16 +155,18 @@ def loss_and_grad_out(out, targets):
 
 # ----------------------------------------------------------------------------- 4. backward, Adam
 
-def backward(theta, cache, g_out):
-    """Gradient of the loss with respect to the flat parameter vector."""
+def backward(theta, cache, g_out, store_bf16=False):
+    """Gradient of the loss with respect to the flat parameter vector.  With store_bf16 the
+    gradients with respect to each layer's pre-activation are rounded to bfloat16 (the GPU
+    network's storage format)."""
     grads = []
-    g = np.asarray(g_out, np.float64)
+    g = _stored(np.asarray(g_out, np.float64), store_bf16)
     params = unpack(np.asarray(theta, np.float64))
     for li in range(len(LAYERS) - 1, -1, -1):
-        _, _, s, relu = LAYERS[li]
+        _, _, s, _ = LAYERS[li]
         w, _ = params[li]
-        h, z = cache[li]
-        dz = g * (z > 0.0) if relu else g
+        h, _ = cache[li]
+        dz = g  # already through this layer's ReLU
         B, H, W, _ = h.shape
         Ho, Wo = dz.shape[1:3]
         hp = np.pad(h, ((0, 0), (1, 1), (1, 1), (0, 0)))
@@ -172,16 +180,18 @@ def backward(theta, cache, g_out):
                 dhp[sl] += np.tensordot(dz, w[:, ky, kx, :], axes=([3], [0]))
         grads.append((dw, dz.sum(axis=(0, 1, 2))))
         g = dhp[:, 1:H + 1, 1:W + 1, :]
+        if li > 0 and LAYERS[li - 1][3]:
+            g = _stored(g * (cache[li - 1][1] > 0.0), store_bf16)
     flat = []
     for dw, db in reversed(grads):
         flat += [dw.ravel(), db]
     return np.concatenate(flat)
 
 
-def loss_and_grad(theta, x, targets):
-    out, cache = forward(theta, x)
+def loss_and_grad(theta, x, targets, store_bf16=False):
+    out, cache = forward(theta, x, store_bf16)
     loss, g = loss_and_grad_out(out, targets)
-    return loss, backward(theta, cache, g)
+    return loss, backward(theta, cache, g, store_bf16)
 
 
 def adam_step(theta, m, v, grad, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):

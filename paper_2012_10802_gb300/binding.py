@@ -7,6 +7,8 @@ There is no CPU fallback: if the library is missing or no GPU is present, calls 
 import ctypes as C
 import os
 
+import numpy as np
+
 import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -89,6 +91,20 @@ SIGNATURES = {
     "pd_aggregate": [_P, _P, _i, _i, _i, _i, _i, _i, _P],
     "pd_disparity": [_P, _P, _i, _i, _i, _P, _i, _P, _P],
     "pd_sgm": [_P, _P, _P, _i, _i, _z, C.POINTER(RoadModel), C.POINTER(Params), _P, _P, _P],
+    "pd_sgm_band": [_P, _P, _P, _i, _i, _z, C.POINTER(RoadModel), C.POINTER(Params), _P, _i,
+                    _P, _P, _P],
+    "pd_cnn_create": [C.POINTER(C.c_void_p), _i, _i, _i, _i],
+    "pd_cnn_destroy": [_P],
+    "pd_cnn_set_params": [_P, _P, _P, _i],
+    "pd_cnn_get_params": [_P, _P, _P, _i],
+    "pd_cnn_forward": [_P, _P, _P, _i, _i, _i, _P],
+    "pd_cnn_loss_grad": [_P, _P, _P, _P, _i, _i, _i, _P, _P],
+    "pd_cnn_train_step": [_P, _P, _P, _P, _i, _i, _i, _f, _P],
+    "pd_band_input": [_P, _P, _P, _i, _i, _z, _P, _P],
+    "pd_band_labels": [_P, _P, _P, _i, _i, _i, _P],
+    "pd_band_tiles": [_P, _P, _i, _i, _i, _i, _P],
+    "pd_sgm_learned": [_P, _P, _P, _P, _i, _i, _z, C.POINTER(RoadModel), C.POINTER(Params), _i,
+                       _P, _P, _P, _P],
     "pd_moments": [_P, _P, _i, _i, _P],
     "pd_transform": [_P, _P, _i, _i, _i, _f, _P, _P],
     "pd_superpixels": [_P, _P, _i, _i, _i, _f, _i, _P, _P, _P, C.POINTER(_i)],
@@ -101,7 +117,8 @@ SIGNATURES = {
     "pd_profile_enable": [_P, _i],
     "pd_profile_read": [_P, C.POINTER(Profile)],
 }
-EXTRA = {"pd_last_error": (C.c_char_p, [_P]), "pd_workspace_bytes": (C.c_size_t, [_P])}
+EXTRA = {"pd_last_error": (C.c_char_p, [_P]), "pd_workspace_bytes": (C.c_size_t, [_P]),
+         "pd_cnn_num_params": (C.c_int, [])}
 
 _lib = None
 
@@ -255,6 +272,141 @@ def pd_sgm(ctx, left, right, model, params, kappa=None, d_int=None, D1=None):
     ctx.check(lib().pd_sgm(ctx.h, _ptr(left), _ptr(right), W, H, W, C.byref(model),
                            C.byref(params), _ptr(kappa), _ptr(d_int), _ptr(D1)))
     return kappa, d_int, D1
+
+
+def pd_sgm_band(ctx, left, right, model, params, tile_lo, band_width=17, kappa=None, d_int=None,
+                D1=None):
+    H, W = left.shape
+    assert tile_lo.dtype == torch.int16 and tuple(tile_lo.shape) == ((H + 15) // 16, (W + 15) // 16)
+    if kappa is None:
+        kappa = ctx.empty((H,), torch.int32)
+    if d_int is None:
+        d_int = ctx.empty((H, W), torch.int16)
+    if D1 is None:
+        D1 = ctx.empty((H, W), torch.float32)
+    ctx.check(lib().pd_sgm_band(ctx.h, _ptr(left), _ptr(right), W, H, W, C.byref(model),
+                                C.byref(params), _ptr(tile_lo), band_width, _ptr(kappa),
+                                _ptr(d_int), _ptr(D1)))
+    return kappa, d_int, D1
+
+
+class Cnn:
+    """Owns one pd_cnn (the band network) sized for max_batch inputs of max_hd x max_wd cells."""
+
+    def __init__(self, device=0, max_batch=1, max_hd=270, max_wd=480):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libpothole needs a CUDA GPU; none is available")
+        h = C.c_void_p()
+        st = lib().pd_cnn_create(C.byref(h), device, max_batch, max_hd, max_wd)
+        if st != PD_OK:
+            raise PdError(st, "pd_cnn_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pd_cnn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pd_cnn_num_params():
+    return int(lib().pd_cnn_num_params())
+
+
+def pd_cnn_set_params(ctx, net, params):
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    ctx.check(lib().pd_cnn_set_params(ctx.h, net.h, a.ctypes.data_as(C.c_void_p), a.size))
+
+
+def pd_cnn_get_params(ctx, net):
+    a = np.empty(pd_cnn_num_params(), np.float32)
+    ctx.check(lib().pd_cnn_get_params(ctx.h, net.h, a.ctypes.data_as(C.c_void_p), a.size))
+    return a
+
+
+def _out_shape(Hd, Wd):
+    return (Hd - 1) // 4 + 1, (Wd - 1) // 4 + 1
+
+
+def pd_cnn_forward(ctx, net, x, out=None):
+    """x: bf16 [B][Hd][Wd][2] (or [Hd][Wd][2]) on the device -> float [B][Ho][Wo][2]."""
+    if x.dim() == 3:
+        x = x.unsqueeze(0)
+    assert x.dtype == torch.bfloat16 and x.is_contiguous()
+    B, Hd, Wd, _ = x.shape
+    Ho, Wo = _out_shape(Hd, Wd)
+    if out is None:
+        out = ctx.empty((B, Ho, Wo, 2), torch.float32)
+    ctx.check(lib().pd_cnn_forward(ctx.h, net.h, _ptr(x), B, Hd, Wd, _ptr(out)))
+    return out
+
+
+def pd_cnn_loss_grad(ctx, net, x, targets):
+    if x.dim() == 3:
+        x = x.unsqueeze(0)
+        targets = targets.unsqueeze(0)
+    B, Hd, Wd, _ = x.shape
+    loss = ctx.empty((1,), torch.float32)
+    grad = ctx.empty((pd_cnn_num_params(),), torch.float32)
+    ctx.check(lib().pd_cnn_loss_grad(ctx.h, net.h, _ptr(x), _ptr(targets), B, Hd, Wd, _ptr(loss),
+                                     _ptr(grad)))
+    return loss, grad
+
+
+def pd_cnn_train_step(ctx, net, x, targets, lr, loss=None):
+    if x.dim() == 3:
+        x = x.unsqueeze(0)
+        targets = targets.unsqueeze(0)
+    B, Hd, Wd, _ = x.shape
+    ctx.check(lib().pd_cnn_train_step(ctx.h, net.h, _ptr(x), _ptr(targets), B, Hd, Wd,
+                                      float(lr), _ptr(loss)))
+    return loss
+
+
+def pd_band_input(ctx, left, right, kappa, x=None):
+    H, W = left.shape
+    if x is None:
+        x = ctx.empty(((H + 3) // 4, (W + 3) // 4, 2), torch.bfloat16)
+    ctx.check(lib().pd_band_input(ctx.h, _ptr(left), _ptr(right), W, H, W, _ptr(kappa), _ptr(x)))
+    return x
+
+
+def pd_band_labels(ctx, d_int, D1, D, targets=None):
+    H, W = d_int.shape
+    if targets is None:
+        targets = ctx.empty(((H + 15) // 16, (W + 15) // 16, 4), torch.float32)
+    ctx.check(lib().pd_band_labels(ctx.h, _ptr(d_int), _ptr(D1), W, H, D, _ptr(targets)))
+    return targets
+
+
+def pd_band_tiles(ctx, cnn_out, D, band_width=17, tile_lo=None):
+    th, tw = cnn_out.shape[-3], cnn_out.shape[-2]
+    if tile_lo is None:
+        tile_lo = ctx.empty((th, tw), torch.int16)
+    ctx.check(lib().pd_band_tiles(ctx.h, _ptr(cnn_out), th, tw, D, band_width, _ptr(tile_lo)))
+    return tile_lo
+
+
+def pd_sgm_learned(ctx, net, left, right, model, params, band_width=17, tile_lo=None, kappa=None,
+                   d_int=None, D1=None):
+    H, W = left.shape
+    if tile_lo is None:
+        tile_lo = ctx.empty(((H + 15) // 16, (W + 15) // 16), torch.int16)
+    if kappa is None:
+        kappa = ctx.empty((H,), torch.int32)
+    if d_int is None:
+        d_int = ctx.empty((H, W), torch.int16)
+    if D1 is None:
+        D1 = ctx.empty((H, W), torch.float32)
+    ctx.check(lib().pd_sgm_learned(ctx.h, net.h, _ptr(left), _ptr(right), W, H, W, C.byref(model),
+                                   C.byref(params), band_width, _ptr(tile_lo), _ptr(kappa),
+                                   _ptr(d_int), _ptr(D1)))
+    return tile_lo, kappa, d_int, D1
 
 
 def pd_moments(ctx, D1, sums=None):

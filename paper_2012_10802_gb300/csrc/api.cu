@@ -201,6 +201,34 @@ pd_status sgm_enqueue(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, in
   return launched(ctx, "pd_sgm");
 }
 
+// Enqueues the band-restricted SGM (no validation; scratch already sized).
+pd_status sgm_band_enqueue(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H,
+                           size_t pitch, const pd_road_model* model, const pd_params* p,
+                           const BandArgs& band, int32_t* kappa, int16_t* d_int, float* D1,
+                           pd_prof_rec* rec) {
+  cudaStream_t s = ctx->stream;
+  SgmScratch sc = sgm_carve(ctx->ws, W, H, p->D, p->paths);
+  int32_t* kap = kappa ? kappa : sc.kappa;
+  size_t N = (size_t)W * H;
+  size_t vol = N * p->D;
+  mark(ctx, rec, 0);
+  launch_kappa(s, W, H, model->order, model->a, cos(model->roll), sin(model->roll),
+               (double)p->delta_pt, kap);
+  launch_census(s, left, W, H, pitch, nullptr, sc.cl);
+  launch_census(s, right, W, H, pitch, kap, sc.cr);
+  launch_cost_band(s, sc.cl, sc.cr, W, H, p->D, band, sc.cost);
+  cudaMemsetAsync(sc.rkeys, 0xff, N * sizeof(uint32_t), s);
+  mark(ctx, rec, 1);
+  launch_aggregate_band(s, sc.cost, W, H, p->D, dir_set(p->paths), p->P1, p->P2, sc.vols, vol,
+                        band);
+  mark(ctx, rec, 2);
+  launch_wta_band(s, sc.vols, p->paths, vol, W, H, p->D, band, d_int, sc.dsub, sc.rkeys);
+  launch_lr_band(s, d_int, sc.dsub, sc.rkeys, kap, W, H, p->D, band, p->lr_tol, D1);
+  mark(ctx, rec, 3);
+  count_launches(ctx, 7);
+  return launched(ctx, "pd_sgm_band");
+}
+
 size_t transform_scratch_bytes(int W, int H) {
   size_t acc = 0;
   carve_size<uint8_t>(acc, moments_scratch_bytes(W, H));
@@ -687,6 +715,57 @@ pd_status pd_sgm(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, 
   PD_TRY(ensure_ws(ctx, sgm_scratch_bytes(W, H, params->D, params->paths)));
   return sgm_enqueue(ctx, left, right, W, H, pitch, model, params, kappa, d_int, D1,
                      prof_begin(ctx));
+}
+
+pd_status pd_sgm_band(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H,
+                      size_t pitch, const pd_road_model* model, const pd_params* params,
+                      const int16_t* tile_lo, int band_width, int32_t* kappa, int16_t* d_int,
+                      float* D1) {
+  PD_TRY(begin(ctx));
+  PD_TRY(check_image(ctx, W, H, pitch));
+  PD_TRY(check_model(ctx, model));
+  PD_TRY(check_sgm_params(ctx, params));
+  PD_REQUIRE(left && right && d_int && D1 && tile_lo, "NULL input or output");
+  PD_REQUIRE(band_width >= 1 && band_width <= params->D, "band width %d must be in 1..D",
+             band_width);
+  PD_TRY(ensure_ws(ctx, sgm_scratch_bytes(W, H, params->D, params->paths)));
+  BandArgs band{tile_lo, (W + 15) / 16, band_width};
+  return sgm_band_enqueue(ctx, left, right, W, H, pitch, model, params, band, kappa, d_int, D1,
+                          prof_begin(ctx));
+}
+
+pd_status pd_sgm_learned(pd_ctx* ctx, pd_cnn* net, const uint8_t* left, const uint8_t* right,
+                         int W, int H, size_t pitch, const pd_road_model* model,
+                         const pd_params* params, int band_width, int16_t* tile_lo,
+                         int32_t* kappa, int16_t* d_int, float* D1) {
+  PD_TRY(begin(ctx));
+  PD_TRY(check_image(ctx, W, H, pitch));
+  PD_TRY(check_model(ctx, model));
+  PD_TRY(check_sgm_params(ctx, params));
+  PD_REQUIRE(left && right && d_int && D1, "NULL input or output");
+  PD_REQUIRE(band_width >= 1 && band_width <= params->D, "band width %d must be in 1..D",
+             band_width);
+  const int Hd = (H + 3) / 4, Wd = (W + 3) / 4, th = (H + 15) / 16, tw = (W + 15) / 16;
+  PD_REQUIRE(cnn_fits(net, 1, Hd, Wd), "the network does not accept a %dx%d input", Wd, Hd);
+  size_t acc = sgm_scratch_bytes(W, H, params->D, params->paths);
+  const size_t x_off = (acc + 255) & ~size_t(255);
+  const size_t t_off = (x_off + (size_t)Hd * Wd * 2 * 2 + 255) & ~size_t(255);
+  PD_TRY(ensure_ws(ctx, t_off + (size_t)th * tw * sizeof(int16_t)));
+  char* ws = static_cast<char*>(ctx->ws);
+  void* x = ws + x_off;
+  int16_t* tl = tile_lo ? tile_lo : reinterpret_cast<int16_t*>(ws + t_off);
+  SgmScratch sc = sgm_carve(ctx->ws, W, H, params->D, params->paths);
+  int32_t* kap = kappa ? kappa : sc.kappa;
+  cudaStream_t s = ctx->stream;
+  launch_kappa(s, W, H, model->order, model->a, cos(model->roll), sin(model->roll),
+               (double)params->delta_pt, kap);
+  launch_band_input(s, left, right, W, H, pitch, kap, x);
+  const float* out = cnn_forward_enqueue(s, net, x, Hd, Wd);
+  launch_band_tiles(s, out, th * tw, params->D, band_width, tl);
+  count_launches(ctx, 11);
+  BandArgs band{tl, tw, band_width};
+  return sgm_band_enqueue(ctx, left, right, W, H, pitch, model, params, band, kap, d_int, D1,
+                          prof_begin(ctx));
 }
 
 pd_status pd_moments(pd_ctx* ctx, const float* D1, int W, int H, int64_t* sums) {

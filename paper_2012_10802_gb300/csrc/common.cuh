@@ -113,6 +113,34 @@ void launch_lr(cudaStream_t s, const int16_t* d_int, const float* dsub, const ui
 
 // ------------------------------------------------------------ transform launchers (dt.cu)
 // Float coefficients of f for the D2 kernel, written by the roll solver on the device.
+// Per-tile disparity windows of the band-restricted search: tile (u/16, v/16) searches
+// [lo, min(lo + width, D)) with lo = min(tile_lo, D - 1), or all of [0, D) where tile_lo < 0.
+struct BandArgs {
+  const int16_t* tile_lo;  // [ceil(H/16)][tw], device
+  int tw;
+  int width;
+};
+
+void launch_cost_band(cudaStream_t s, const uint32_t* cl, const uint32_t* cr, int W, int H, int D,
+                      const BandArgs& band, uint8_t* cost);
+void launch_aggregate_band(cudaStream_t s, const uint8_t* cost_il, int W, int H, int D,
+                           const DirSet& dirs, int P1, int P2, uint8_t* out, size_t vol_bytes,
+                           const BandArgs& band);
+void launch_wta_band(cudaStream_t s, const uint8_t* vols, int ndirs, size_t vol_bytes, int W,
+                     int H, int D, const BandArgs& band, int16_t* d_int, float* dsub,
+                     uint32_t* rkeys);
+void launch_lr_band(cudaStream_t s, const int16_t* d_int, const float* dsub, const uint32_t* rkeys,
+                    const int32_t* kappa, int W, int H, int D, const BandArgs& band, int lr_tol,
+                    float* D1);
+
+// The band network (cnn.cu).
+bool cnn_fits(const pd_cnn* net, int B, int Hd, int Wd);
+const float* cnn_forward_enqueue(cudaStream_t s, pd_cnn* net, const void* x, int Hd, int Wd);
+void launch_band_input(cudaStream_t s, const uint8_t* left, const uint8_t* right, int W, int H,
+                       size_t pitch, const int32_t* kappa, void* x);
+void launch_band_tiles(cudaStream_t s, const float* cnn_out, int n, int D, int band_width,
+                       int16_t* tile_lo);
+
 struct RoadCoefF {
   float c, s, a0, a1, a2, uc, vc, pad;
 };

@@ -171,3 +171,49 @@ def true_model(scene: Scene, order=2):
     """The scene's road model in the (order, a, roll) form of Sec. II-A Eq. (3)."""
     a = scene.a if order == 2 else (scene.a[0], scene.a[1], 0.0)
     return order, tuple(float(x) for x in a), float(scene.roll)
+
+
+def render_torch(scene: Scene, device="cuda"):
+    """The same scene model as render(), drawn on a CUDA device with torch's generator (seeded by
+    the scene's seed): for producing many large training pairs quickly.  Returns (left, right)
+    uint8 device tensors of shape (H, W).  The images follow render()'s recipe but not its
+    random numbers."""
+    import torch
+
+    W, H = scene.W, scene.H
+    g = torch.Generator(device=device)
+    g.manual_seed(int(scene.seed))
+    noise = torch.randint(0, 256, (H + 2, W + 2), generator=g, device=device, dtype=torch.int32)
+    box = torch.zeros((H, W), dtype=torch.int32, device=device)
+    for dy in range(3):
+        for dx in range(3):
+            box += noise[dy:dy + H, dx:dx + W]
+    left = torch.div(box + 4, 9, rounding_mode="floor").to(torch.uint8)
+
+    v = torch.arange(H, device=device, dtype=torch.float64)[:, None].expand(H, W)
+    x = torch.arange(W, device=device, dtype=torch.float64)[None, :].expand(H, W)
+    uc, vc = (W - 1) / 2.0, (H - 1) / 2.0
+    cs, sn = float(np.cos(scene.roll)), float(np.sin(scene.roll))
+    a0, a1, a2 = scene.a
+
+    def disp(u):
+        vp = (v - vc) * cs - (u - uc) * sn + vc
+        d = a0 + a1 * vp + a2 * vp * vp
+        for p in scene.potholes:
+            rho = torch.sqrt(((u - p.cu) / p.ax) ** 2 + ((v - p.cv) / p.ay) ** 2)
+            d = d - torch.where(rho < 1.0, p.depth * 0.5 * (1.0 + torch.cos(np.pi * torch.clamp(rho, max=1.0))),
+                                torch.zeros_like(rho))
+        return d
+
+    u = x + disp(x)
+    for _ in range(3):
+        u = x + disp(u)
+    u = torch.clamp(u, 0.0, W - 1.0)
+    u0 = torch.floor(u).to(torch.int64)
+    u1 = torch.clamp(u0 + 1, max=W - 1)
+    t = u - u0
+    lf = left.to(torch.float64)
+    val = (1.0 - t) * torch.gather(lf, 1, u0) + t * torch.gather(lf, 1, u1)
+    val = val + torch.randn((H, W), generator=g, device=device, dtype=torch.float64) * scene.noise_sigma
+    right = torch.clamp(torch.round(val), 0, 255).to(torch.uint8)
+    return left.contiguous(), right.contiguous()

@@ -1,0 +1,219 @@
+"""The band network on the GPU (bf16 tensor-core convolutions, fp32 accumulation) against the
+float64 oracle run on the same bf16-rounded parameters and layer inputs: forward outputs and every
+layer's loss gradients within 2e-3 relative norm (and within a few percent of the exact float64
+network); the network input, training labels and tile windows bit-exact; the Adam step bounded
+as Adam's first step must be."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import band_cnn as bc
+from paper_2012_10802_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2012_10802_gb300 import binding, build
+    build.build()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(B):
+    c = B.Context(0)
+    yield c
+    c.close()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def _theta(seed):
+    th = bc.init_params(seed)
+    rng = np.random.default_rng(seed)
+    nb = 0
+    for ci, co, _, _ in bc.LAYERS:        # small non-zero biases
+        nb += co * 9 * ci
+        th[nb:nb + co] = rng.normal(0, 0.1, co)
+        nb += co
+    return bc.bf16_round(th)
+
+
+def _input(seed, Bn, Hd, Wd):
+    rng = np.random.default_rng(seed)
+    return bc.bf16_round(rng.normal(0, 1, size=(Bn, Hd, Wd, 2)).astype(np.float32))
+
+
+def _targets(seed, Bn, Ho, Wo):
+    rng = np.random.default_rng(seed)
+    t = np.zeros((Bn, Ho, Wo, 4), np.float32)
+    t[..., 0] = rng.integers(0, 40, size=(Bn, Ho, Wo))
+    t[..., 1] = rng.integers(0, 2, size=(Bn, Ho, Wo))
+    t[..., 2] = (rng.random((Bn, Ho, Wo)) < 0.8)
+    t[..., 3] = 1.0
+    return t
+
+
+def _to_dev_bf16(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(torch.bfloat16).cuda()
+
+
+@pytest.mark.parametrize("Bn,Hd,Wd", [(1, 270, 480), (3, 37, 53), (2, 8, 8), (1, 5, 131)])
+def test_forward_matches_oracle(B, ctx, Bn, Hd, Wd):
+    th = _theta(1)
+    x = _input(2, Bn, Hd, Wd)
+    net = B.Cnn(0, max_batch=Bn, max_hd=Hd, max_wd=Wd)
+    B.pd_cnn_set_params(ctx, net, th)
+    out = B.pd_cnn_forward(ctx, net, _to_dev_bf16(x))
+    torch.cuda.synchronize()
+    ref_bf, _ = bc.forward(th, x, store_bf16=True)   # parity: same bf16 layer inputs
+    assert out.shape == ref_bf.shape
+    assert _rel(out.cpu().numpy(), ref_bf) < 2e-3
+    ref, _ = bc.forward(th, x)                          # the exact network
+    assert _rel(out.cpu().numpy(), ref) < 2e-2
+    net.close()
+
+
+@pytest.mark.parametrize("Bn,Hd,Wd", [(2, 68, 120), (1, 270, 480), (3, 21, 35)])
+def test_loss_gradient_matches_oracle(B, ctx, Bn, Hd, Wd):
+    th = _theta(3)
+    x = _input(4, Bn, Hd, Wd)
+    Ho, Wo = (Hd + 3) // 4, (Wd + 3) // 4
+    t = _targets(5, Bn, Ho, Wo)
+    net = B.Cnn(0, max_batch=Bn, max_hd=Hd, max_wd=Wd)
+    B.pd_cnn_set_params(ctx, net, th)
+    loss, grad = B.pd_cnn_loss_grad(ctx, net, _to_dev_bf16(x), torch.from_numpy(t).cuda())
+    torch.cuda.synchronize()
+    g = grad.cpu().numpy()
+    # Parity: the oracle on the same bf16-rounded weights and layer inputs (activations and
+    # back-propagated gradients stored as bf16, as the GPU stores them): only the accumulation
+    # order differs, so every layer's weight and bias gradients agree to 2e-3.
+    bf_loss, bf_grad = bc.loss_and_grad(th, x, t, store_bf16=True)
+    assert abs(loss.item() - bf_loss) <= 1e-4 * abs(bf_loss)
+    k = 0
+    for li, (ci, co, _, _) in enumerate(bc.LAYERS):
+        nw = co * 9 * ci
+        for sl in (slice(k, k + nw), slice(k + nw, k + nw + co)):
+            assert _rel(g[sl], bf_grad[sl]) < 2e-3, (li, _rel(g[sl], bf_grad[sl]))
+        k += nw + co
+    # Against the exact float64 network the bf16 storage costs a few percent at most.
+    ref_loss, ref_grad = bc.loss_and_grad(th, x, t)
+    assert abs(loss.item() - ref_loss) <= 2e-2 * abs(ref_loss)
+    assert _rel(g, ref_grad) < 5e-2
+    net.close()
+
+
+def test_adam_first_step(B, ctx):
+    """Adam's first step moves every parameter by lr * g / (|g| + eps): at most lr, against the
+    sign of the gradient."""
+    th = _theta(6)
+    Hd, Wd = 40, 64
+    x = _input(7, 2, Hd, Wd)
+    t = _targets(8, 2, 10, 16)
+    net = B.Cnn(0, max_batch=2, max_hd=Hd, max_wd=Wd)
+    B.pd_cnn_set_params(ctx, net, th)
+    lr = 1e-3
+    B.pd_cnn_train_step(ctx, net, _to_dev_bf16(x), torch.from_numpy(t).cuda(), lr)
+    after = B.pd_cnn_get_params(ctx, net)
+    _, g = bc.loss_and_grad(th, x, t)
+    step = after.astype(np.float64) - th
+    assert np.all(np.abs(step) <= lr * (1 + 1e-3) + 1e-7)
+    big = np.abs(g) > 1e-2 * np.abs(g).max()
+    assert np.mean(np.sign(step[big]) == -np.sign(g[big])) > 0.99
+    assert np.allclose(np.abs(step[big]), lr, rtol=1e-2)
+    net.close()
+
+
+def test_training_lowers_the_loss(B, ctx):
+    """A few hundred Adam steps on a fixed batch drive the loss well below its start."""
+    Hd, Wd = 32, 48
+    x = _input(9, 4, Hd, Wd)
+    t = _targets(10, 4, 8, 12)
+    net = B.Cnn(0, max_batch=4, max_hd=Hd, max_wd=Wd)
+    B.pd_cnn_set_params(ctx, net, bc.init_params(11))
+    xd, td = _to_dev_bf16(x), torch.from_numpy(t).cuda()
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    B.pd_cnn_train_step(ctx, net, xd, td, 3e-3, loss)
+    first = loss.item()
+    for _ in range(300):
+        B.pd_cnn_train_step(ctx, net, xd, td, 3e-3, loss)
+    torch.cuda.synchronize()
+    assert loss.item() < 0.5 * first
+    net.close()
+
+
+@pytest.mark.parametrize("W,H", [(1920, 1080), (97, 61), (30, 17)])
+def test_band_input_matches_oracle(B, ctx, orc, W, H):
+    sc = synth.road_scaled(W, H, 5)
+    left, right = synth.render(sc)
+    m = synth.true_model(sc)
+    kap = orc.kappa(orc.RoadModel.make(*m), W, H, 10.0)
+    ref = bc.band_input(left, right, kap)
+    x = B.pd_band_input(ctx, torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda(),
+                        torch.from_numpy(kap).cuda())
+    torch.cuda.synchronize()
+    assert np.array_equal(x.float().cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("W,H,D", [(200, 100, 128), (1920, 1080, 128), (50, 37, 32)])
+def test_labels_match_oracle(B, ctx, W, H, D):
+    rng = np.random.default_rng(W)
+    th0, tw0 = H // 16 + 1, W // 16 + 1
+    base = rng.integers(0, D, size=(th0, tw0))                 # one level per tile, then noise:
+    spread = rng.choice([0, 3, 9], size=(th0, tw0))            # +-spread around it,
+    outl = rng.choice([0.0, 0.003, 0.02], size=(th0, tw0))     # and this fraction of outliers
+    up = lambda a: np.kron(a, np.ones((16, 16), a.dtype))[:H, :W]
+    d = up(base) + np.rint(rng.uniform(-1, 1, (H, W)) * up(spread)).astype(np.int64)
+    d = np.where(rng.random((H, W)) < up(outl), rng.integers(0, D, size=(H, W)), d)
+    d = np.clip(d, 0, D - 1).astype(np.int16)
+    D1 = np.where(rng.random((H, W)) < 0.3, -1.0, d + 0.25).astype(np.float32)
+    D1[:, : W // 10] = -1.0
+    th, tw = (H + 15) // 16, (W + 15) // 16
+    ref = bc.labels(d, D1, th, tw)
+    t = B.pd_band_labels(ctx, torch.from_numpy(d).cuda(), torch.from_numpy(D1).cuda(), D)
+    torch.cuda.synchronize()
+    assert np.array_equal(t.cpu().numpy(), ref)
+    assert 0 < ref[..., 1].sum() < th * tw
+
+
+def test_tiles_match_oracle(B, ctx):
+    rng = np.random.default_rng(12)
+    out = np.empty((68, 120, 2), np.float32)
+    out[..., 0] = rng.uniform(-1, 10, size=(68, 120))
+    out[..., 1] = rng.normal(2.0, 1.5, size=(68, 120))
+    out[0, :4, 1] = [np.float32(math.log(9.0)), np.nextafter(np.float32(math.log(9.0)), np.float32(0)), 5, 5]
+    out[0, 2:4, 0] = [2.5 / 16 + 0.5, 0.15625]          # rint ties
+    for D, band in [(128, 17), (32, 17), (64, 5), (16, 16)]:
+        ref = bc.tile_windows(out, D, band)
+        tl = B.pd_band_tiles(ctx, torch.from_numpy(out).cuda(), D, band)
+        torch.cuda.synchronize()
+        assert np.array_equal(tl.cpu().numpy(), ref), (D, band)
+
+
+def test_learned_path_is_the_composition(B, ctx):
+    """pd_sgm_learned = pd_band_input, pd_cnn_forward, pd_band_tiles and pd_sgm_band."""
+    W, H, D = 640, 480, 128
+    sc = synth.road_scaled(W, H, 20001)
+    left, right = synth.render(sc)
+    l, r = torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda()
+    model = B.RoadModel.make(*synth.true_model(sc))
+    p = B.default_params(D=D)
+    net = B.Cnn(0, 1, (H + 3) // 4, (W + 3) // 4)
+    th = bc.init_params(13)
+    th[-1] = 4.0                                        # confident everywhere
+    th[-2] = 1.0                                        # centre ~ 16 px
+    B.pd_cnn_set_params(ctx, net, th)
+    tl, kap, d, D1 = B.pd_sgm_learned(ctx, net, l, r, model, p, 17)
+    x = B.pd_band_input(ctx, l, r, kap)
+    out = B.pd_cnn_forward(ctx, net, x)
+    tl2 = B.pd_band_tiles(ctx, out[0], D, 17)
+    _, d2, D12 = B.pd_sgm_band(ctx, l, r, model, p, tl2, 17)
+    torch.cuda.synchronize()
+    assert torch.equal(tl, tl2) and torch.equal(d, d2) and torch.equal(D1, D12)
+    assert (tl >= 0).float().mean().item() > 0.5
+    net.close()
