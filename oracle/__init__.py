@@ -66,6 +66,8 @@ def _declare(L):
         "or_superpixel_mean": (None, [_P, _P, _i, _i, _i, _P]),
         "or_threshold": (_i, [_P, _P, _i, _i, _f, _i, C.POINTER(_d), C.POINTER(_d), _P]),
         "or_mask": (None, [_P, _i, _i, _d, _P]),
+        "or_ccl": (_i, [_P, _i, _i, _i, _P]),
+        "or_components": (None, [_P, _P, _i, _i, _i, _P]),
         "or_band_windows": (None, [_P, _i, _i, _i, _i, _P, _P]),
         "or_aggregate_band": (None, [_P, _P, _P, _i, _i, _i, _i, _i, _i, _P]),
         "or_disparity_band": (None, [_P, _P, _P, _i, _i, _i, _P, _i, _P, _P]),
@@ -348,3 +350,27 @@ def sgm_band(left, right, model, p: Params, tile_lo, band=17):
     S = aggregate_band(cst, lo, hi, p.paths, p.P1, p.P2)
     d_int, D1 = disparity_band(S, lo, hi, kap, p.lr_tol)
     return {"kappa": kap, "lo": lo, "hi": hi, "S": S, "d_int": d_int, "D1": D1}
+
+
+# ----------------------------------------------------------------------------- Sec. II-E CCL
+
+COMPONENT_FIELDS = ("label", "count", "umin", "vmin", "umax", "vmax", "sum_u", "sum_v",
+                    "superpixels", "corner", "single", "fake")
+
+
+def ccl(mask, conn=8):
+    """Connected components of the mask: (labels [H][W] int32, number of components)."""
+    m = _c(mask, np.uint8)
+    H, W = m.shape
+    labels = np.empty((H, W), np.int32)
+    n = lib().or_ccl(_ptr(m), W, H, conn, _ptr(labels))
+    return labels, n
+
+
+def components(labels, sp_labels, n):
+    """Per-component statistics and the fake-pothole flags, [n][12] int64 (COMPONENT_FIELDS)."""
+    lab = _c(labels, np.int32)
+    H, W = lab.shape
+    out = np.zeros((max(n, 1), 12), np.int64)
+    lib().or_components(_ptr(lab), _ptr(_c(sp_labels, np.int32)), W, H, n, _ptr(out))
+    return out[:n]

@@ -19,6 +19,9 @@
  *   R7 roll: closed form for the linear model, grid + golden section for the quadratic one;
  *   R8 SLIC grid/tie rules, fixed iteration count;
  *   R9 threshold regions on the diagonal with exact (fixed-point) g; t_s from the road mean;
+ *   R14 connected components of the mask: 8- or 4-connectivity, labelled by their smallest
+ *       raster index (Sec. II-E names CCL only);
+ *   R15 fake potholes (Sec. III-B): centroid in a corner cell of an 8 x 8 split, or one superpixel;
  *   R10 (band SGM, beyond the paper) per-16x16-tile windows [lo, lo + band) clipped to [0, D),
  *       L = +infinity outside the window, minima of Eq. (8) over the previous pixel's window,
  *       winners and right views over in-window candidates, valid pixels need u >= hi - 1.
@@ -830,4 +833,94 @@ void or_disparity_band(const uint16_t* S, const int16_t* lo, const int16_t* hi, 
     }
   }
   free(dright);
+}
+
+/* --------------------------------------------------- Sec. II-E: connected component labelling */
+
+/* Reading R14: the pothole mask's connected components, with 8- or 4-connectivity (the paper
+ * names CCL without fixing it), each labelled by the smallest raster index p = v W + u among its
+ * pixels; breadth-first search from every unlabelled mask pixel in raster order.  Pixels outside
+ * the mask get -1.  Returns the number of components. */
+int or_ccl(const uint8_t* mask, int W, int H, int conn, int32_t* labels) {
+  size_t n = (size_t)W * H;
+  int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * (n ? n : 1));
+  int count = 0;
+  for (size_t p = 0; p < n; ++p) labels[p] = -1;
+  for (size_t p = 0; p < n; ++p) {
+    if (!mask[p] || labels[p] >= 0) continue;
+    ++count;
+    size_t head = 0, tail = 0;
+    labels[p] = (int32_t)p;
+    queue[tail++] = (int32_t)p;
+    while (head < tail) {
+      int q = queue[head++];
+      int u = q % W, v = q / W;
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          if (dx == 0 && dy == 0) continue;
+          if (conn == 4 && dx != 0 && dy != 0) continue;
+          int x = u + dx, y = v + dy;
+          if (x < 0 || x >= W || y < 0 || y >= H) continue;
+          size_t r = (size_t)y * W + x;
+          if (mask[r] && labels[r] < 0) {
+            labels[r] = (int32_t)p;
+            queue[tail++] = (int32_t)r;
+          }
+        }
+    }
+  }
+  free(queue);
+  return count;
+}
+
+/* Per-component statistics in the order of the components' labels, and the fake-pothole rule
+ * (Sec. III-B: detections at a corner of the image or made of a single superpixel are fake).
+ * Reading R15: a component lies at a corner when its centroid falls in one of the four corner
+ * cells of the image split 8 x 8 (u < W/8 or u >= 7W/8, and v < H/8 or v >= 7H/8, compared
+ * exactly as 8 sum_u < W n, ...); it is made of one superpixel when all its pixels carry the same
+ * SLIC label.  out: per component 12 int64 values: label, pixel count, u min, v min, u max, v max,
+ * sum u, sum v, superpixels (1, or 2 meaning two or more), corner, single, fake. */
+void or_components(const int32_t* labels, const int32_t* sp, int W, int H, int ncomp,
+                   int64_t* out) {
+  size_t n = (size_t)W * H;
+  int k = 0;
+  for (size_t p = 0; p < n && k < ncomp; ++p) {
+    if (labels[p] != (int32_t)p) continue;
+    int64_t* o = out + (size_t)k * 12;
+    int64_t cnt = 0, su = 0, sv = 0;
+    int umin = W, vmin = H, umax = -1, vmax = -1;
+    int32_t first_sp = 0;
+    int multi = 0;
+    for (size_t q = p; q < n; ++q) {
+      if (labels[q] != (int32_t)p) continue;
+      int u = (int)(q % W), v = (int)(q / W);
+      if (cnt == 0)
+        first_sp = sp[q];
+      else if (sp[q] != first_sp)
+        multi = 1;
+      ++cnt;
+      su += u;
+      sv += v;
+      if (u < umin) umin = u;
+      if (u > umax) umax = u;
+      if (v < vmin) vmin = v;
+      if (v > vmax) vmax = v;
+    }
+    int left = 8 * su < (int64_t)W * cnt, right = 8 * su >= (int64_t)7 * W * cnt;
+    int top = 8 * sv < (int64_t)H * cnt, bottom = 8 * sv >= (int64_t)7 * H * cnt;
+    int corner = (left || right) && (top || bottom);
+    o[0] = (int64_t)p;
+    o[1] = cnt;
+    o[2] = umin;
+    o[3] = vmin;
+    o[4] = umax;
+    o[5] = vmax;
+    o[6] = su;
+    o[7] = sv;
+    o[8] = multi ? 2 : 1;
+    o[9] = corner;
+    o[10] = !multi;
+    o[11] = corner || !multi;
+    ++k;
+  }
 }

@@ -105,6 +105,13 @@ void or_aggregate_band(const uint8_t* cost, const int16_t* lo, const int16_t* hi
 void or_disparity_band(const uint16_t* S, const int16_t* lo, const int16_t* hi, int W, int H, int D,
                        const int32_t* kappa, int lr_tol, int16_t* d_int, float* D1);
 
+/* Sec. II-E connected components of the mask (readings R14, R15): labels = smallest raster index
+ * of the component or -1; returns the component count.  or_components writes 12 int64 per
+ * component (label, count, u/v min, u/v max, sum u, sum v, superpixels, corner, single, fake). */
+int or_ccl(const uint8_t* mask, int W, int H, int conn, int32_t* labels);
+void or_components(const int32_t* labels, const int32_t* sp, int W, int H, int ncomp,
+                   int64_t* out);
+
 /* Test-harness helpers: the size of or_moment_sums, and its 23 sums as (low, high) 64-bit pairs. */
 size_t or_moment_sums_size(void);
 void or_moments_export(const or_moment_sums* mom, int64_t* out);
