@@ -23,7 +23,7 @@ HERE = ROOT
 sys.path.insert(0, ROOT)
 
 W_, H_, D_, PATHS_ = 1280, 720, 128, 8
-WORKLOAD = "road_1280x720_d128_8paths: warp+SGM+transform+SLIC(1000,10,10)+threshold+mask"
+WORKLOAD = "road_1280x720_d128_8paths: warp+SGM+transform+SLIC(1000,10,10)+threshold+mask+components"
 METRIC = "SGM Mdisp/s (W*H*D/s) at 1280x720 D=128, 8 paths, whole path per step"
 # Aggregation ALU view: the recurrence needs 4 u16 lane-ops per (pixel, disparity, path) in the
 # packed DPX form (3-input min, add-min, add cost minus previous minimum, running min); peak = 64
@@ -113,7 +113,7 @@ def measured_peaks():
         return {}
 
 
-AGG_SOURCES = ("sgm.cu", "sgm_body.cuh", "common.cuh")
+AGG_SOURCES = ("sgm.cu", "sgm_body.cuh")
 
 
 def agg_source_sha256():

@@ -70,6 +70,18 @@ typedef struct {
   int threshold_mode; /* 0: t_s = road mean - delta_pd [0]; 1: t_s = t_r - delta_pd */
 } pd_params;
 
+/* One connected component of the pothole mask (56 bytes). */
+typedef struct {
+  int32_t label;        /* the component's smallest raster index v * W + u */
+  int32_t count;        /* pixels */
+  int32_t umin, vmin, umax, vmax;
+  int64_t sum_u, sum_v; /* centroid = sum / count */
+  int32_t superpixels;  /* 1, or 2 meaning two or more */
+  int32_t corner;       /* centroid in a corner cell of the image split 8 x 8 */
+  int32_t single;       /* all pixels in one superpixel */
+  int32_t fake;         /* corner or single (Sec. III-B) */
+} pd_component;
+
 /* Device-side outputs of pd_run_pipeline (all caller-owned device buffers; any may be NULL
  * except where noted). */
 typedef struct {
@@ -82,6 +94,12 @@ typedef struct {
   float* D3;               /* [H][W] superpixel-clustered transformed disparity (required) */
   double* thresholds;      /* [2]: t_r, t_s (device) */
   uint8_t* mask;           /* [H][W] pothole mask (required) */
+  /* Connected components of the mask (pd_components); components == NULL skips that step. */
+  int32_t* components;     /* [H][W] component numbers, -1 outside the mask */
+  pd_component* comps;     /* up to max_comps records */
+  int32_t max_comps;
+  int32_t connectivity;    /* 8 or 4; 0 means 8 */
+  int32_t* n_comps;        /* one int: the number of components, or -1 (see pd_components) */
 } pd_outputs;
 
 /* Per-stage device times of the last pd_run_pipeline call, in milliseconds (host struct). */
@@ -288,6 +306,21 @@ pd_status pd_batch_config(pd_ctx* ctx, size_t scratch_budget_bytes, int use_grap
  * context to pass its table upload before reusing the host staging buffer. */
 pd_status pd_sgm_batch(pd_ctx* ctx, const pd_pair* pairs, int n, const pd_params* params);
 
+/* ------------------------------------------- Sec. II-E: connected components of the mask */
+
+
+/* Sec. II-E "different potholes are labeled using connect component labeling", and Sec. III-B's
+ * rule that detections at a corner of the image or made of one superpixel are fake.  Components
+ * of the mask pixels (mask != 0) with 8- or 4-connectivity, numbered 0, 1, ... in the raster
+ * order of their first pixel.  labels: int32 [H][W], the component number or -1; comps: up to
+ * max_comps records (device); n_comps: one int (device), the number of components (possibly
+ * more than max_comps, whose records are then not written), or -1 if the union-find exceeded its
+ * iteration limit.  mask: uint8 [H][W]; sp_labels: int32 [H][W] superpixel labels (as written
+ * by pd_superpixels). */
+pd_status pd_components(pd_ctx* ctx, const uint8_t* mask, const int32_t* sp_labels, int W, int H,
+                        int connectivity, int32_t* labels, pd_component* comps, int max_comps,
+                        int* n_comps);
+
 /* -------------------------------------- learned disparity band (an extension of the paper) */
 
 /* Sec. II-A and II-B with the disparity search of each 16x16 tile restricted to a window:
@@ -372,8 +405,10 @@ pd_status pd_sgm_learned(pd_ctx* ctx, pd_cnn* net, const uint8_t* left, const ui
 
 /* -------------------------------------------------------------------------- whole path */
 
-/* pd_sgm, pd_transform, pd_superpixels and pd_pothole_mask in sequence on one stream.
- * times (host, may be NULL) receives per-stage device times (this synchronises the stream). */
+/* pd_sgm, pd_transform, pd_superpixels, pd_pothole_mask and (when out->components is set)
+ * pd_components in sequence on one stream.  times (host, may be NULL) receives per-stage device
+ * times (this synchronises the stream); mask_ms covers the threshold, the mask and the
+ * components. */
 pd_status pd_run_pipeline(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H,
                           size_t pitch, const pd_road_model* model, const pd_params* params,
                           const pd_outputs* out, pd_stage_times* times);

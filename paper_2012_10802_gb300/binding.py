@@ -54,7 +54,9 @@ class Params(C.Structure):
 class Outputs(C.Structure):
     _fields_ = [("kappa", C.c_void_p), ("d_int", C.c_void_p), ("D1", C.c_void_p),
                 ("fitted", C.c_void_p), ("D2", C.c_void_p), ("labels", C.c_void_p),
-                ("D3", C.c_void_p), ("thresholds", C.c_void_p), ("mask", C.c_void_p)]
+                ("D3", C.c_void_p), ("thresholds", C.c_void_p), ("mask", C.c_void_p),
+                ("components", C.c_void_p), ("comps", C.c_void_p), ("max_comps", C.c_int32),
+                ("connectivity", C.c_int32), ("n_comps", C.c_void_p)]
 
 
 class StageTimes(C.Structure):
@@ -105,6 +107,7 @@ SIGNATURES = {
     "pd_band_tiles": [_P, _P, _i, _i, _i, _i, _P],
     "pd_sgm_learned": [_P, _P, _P, _P, _i, _i, _z, C.POINTER(RoadModel), C.POINTER(Params), _i,
                        _P, _P, _P, _P],
+    "pd_components": [_P, _P, _P, _i, _i, _i, _P, _P, _i, _P],
     "pd_moments": [_P, _P, _i, _i, _P],
     "pd_transform": [_P, _P, _i, _i, _i, _f, _P, _P],
     "pd_superpixels": [_P, _P, _i, _i, _i, _f, _i, _P, _P, _P, C.POINTER(_i)],
@@ -290,6 +293,27 @@ def pd_sgm_band(ctx, left, right, model, params, tile_lo, band_width=17, kappa=N
     return kappa, d_int, D1
 
 
+COMPONENT_DTYPE = np.dtype([("label", np.int32), ("count", np.int32), ("umin", np.int32),
+                            ("vmin", np.int32), ("umax", np.int32), ("vmax", np.int32),
+                            ("sum_u", np.int64), ("sum_v", np.int64), ("superpixels", np.int32),
+                            ("corner", np.int32), ("single", np.int32), ("fake", np.int32)])
+
+
+def pd_components(ctx, mask, sp_labels, connectivity=8, max_comps=4096, labels=None):
+    """Connected components of the mask: (labels [H][W] int32 device tensor, host array of
+    component records (COMPONENT_DTYPE), component count).  Synchronises the stream."""
+    H, W = mask.shape
+    if labels is None:
+        labels = ctx.empty((H, W), torch.int32)
+    comps = ctx.empty((max(max_comps, 1) * COMPONENT_DTYPE.itemsize,), torch.uint8)
+    n = ctx.empty((1,), torch.int32)
+    ctx.check(lib().pd_components(ctx.h, _ptr(mask), _ptr(sp_labels), W, H, connectivity,
+                                  _ptr(labels), _ptr(comps), max_comps, _ptr(n)))
+    count = int(n.item())
+    recs = comps.cpu().numpy().view(COMPONENT_DTYPE)[:max(0, min(count, max_comps))]
+    return labels, recs, count
+
+
 class Cnn:
     """Owns one pd_cnn (the band network) sized for max_batch inputs of max_hd x max_wd cells."""
 
@@ -454,18 +478,33 @@ def pd_pothole_mask(ctx, D2, D1, D3, delta_pd, mode=0, mask=None, thresholds=Non
     return mask, thresholds
 
 
-def make_outputs(ctx, W, H):
-    """Allocates every pd_outputs buffer for a W x H frame; returns (Outputs, dict of tensors)."""
+def make_outputs(ctx, W, H, components=True, max_comps=4096, connectivity=8):
+    """Allocates every pd_outputs buffer for a W x H frame (with the connected components unless
+    components=False); returns (Outputs, dict of tensors)."""
     t = {"kappa": ctx.empty((H,), torch.int32), "d_int": ctx.empty((H, W), torch.int16),
          "D1": ctx.empty((H, W), torch.float32),
          "fitted": ctx.empty((C.sizeof(RoadModel),), torch.uint8),
          "D2": ctx.empty((H, W), torch.float32), "labels": ctx.empty((H, W), torch.int32),
          "D3": ctx.empty((H, W), torch.float32), "thresholds": ctx.empty((2,), torch.float64),
          "mask": ctx.empty((H, W), torch.uint8)}
+    if components:
+        t["components"] = ctx.empty((H, W), torch.int32)
+        t["comps"] = ctx.empty((max(max_comps, 1) * COMPONENT_DTYPE.itemsize,), torch.uint8)
+        t["n_comps"] = ctx.empty((1,), torch.int32)
     o = Outputs()
     for k, v in t.items():
         setattr(o, k, v.data_ptr())
+    o.max_comps = max_comps if components else 0
+    o.connectivity = connectivity
     return o, t
+
+
+def component_records(outputs):
+    """Host copy of the component records written by pd_run_pipeline (synchronises)."""
+    _, t = outputs
+    n = int(t["n_comps"].item())
+    cap = t["comps"].numel() // COMPONENT_DTYPE.itemsize
+    return t["comps"].cpu().numpy().view(COMPONENT_DTYPE)[:max(0, min(n, cap))], n
 
 
 def pd_run_pipeline(ctx, left, right, model, params, outputs, times=False):

@@ -728,6 +728,7 @@ pd_status pd_sgm_band(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, in
   PD_REQUIRE(left && right && d_int && D1 && tile_lo, "NULL input or output");
   PD_REQUIRE(band_width >= 1 && band_width <= params->D, "band width %d must be in 1..D",
              band_width);
+  PD_REQUIRE(kCensusBits + 2 * params->P2 <= 255, "the band search needs 24 + 2 P2 <= 255");
   PD_TRY(ensure_ws(ctx, sgm_scratch_bytes(W, H, params->D, params->paths)));
   BandArgs band{tile_lo, (W + 15) / 16, band_width};
   return sgm_band_enqueue(ctx, left, right, W, H, pitch, model, params, band, kappa, d_int, D1,
@@ -745,6 +746,7 @@ pd_status pd_sgm_learned(pd_ctx* ctx, pd_cnn* net, const uint8_t* left, const ui
   PD_REQUIRE(left && right && d_int && D1, "NULL input or output");
   PD_REQUIRE(band_width >= 1 && band_width <= params->D, "band width %d must be in 1..D",
              band_width);
+  PD_REQUIRE(kCensusBits + 2 * params->P2 <= 255, "the band search needs 24 + 2 P2 <= 255");
   const int Hd = (H + 3) / 4, Wd = (W + 3) / 4, th = (H + 15) / 16, tw = (W + 15) / 16;
   PD_REQUIRE(cnn_fits(net, 1, Hd, Wd), "the network does not accept a %dx%d input", Wd, Hd);
   size_t acc = sgm_scratch_bytes(W, H, params->D, params->paths);
@@ -819,6 +821,23 @@ pd_status pd_pothole_mask(pd_ctx* ctx, const float* D2, const float* D1, const f
   return launched(ctx, "pd_pothole_mask");
 }
 
+pd_status pd_components(pd_ctx* ctx, const uint8_t* mask, const int32_t* sp_labels, int W, int H,
+                        int connectivity, int32_t* labels, pd_component* comps, int max_comps,
+                        int* n_comps) {
+  PD_TRY(begin(ctx));
+  PD_TRY(check_image(ctx, W, H, (size_t)W));
+  PD_REQUIRE(mask && sp_labels && labels && n_comps, "NULL input or output");
+  PD_REQUIRE(connectivity == 4 || connectivity == 8, "connectivity %d must be 4 or 8",
+             connectivity);
+  PD_REQUIRE(max_comps >= 0 && (max_comps == 0 || comps), "max_comps %d needs a component buffer",
+             max_comps);
+  if (max_comps > W * H) max_comps = W * H;  // no mask has more components than pixels
+  PD_TRY(ensure_ws(ctx, ccl_scratch_bytes(W, H, max_comps)));
+  count_launches(ctx, launch_ccl(ctx->stream, mask, sp_labels, W, H, connectivity, labels, comps,
+                                 max_comps, n_comps, ctx->ws));
+  return launched(ctx, "pd_components");
+}
+
 pd_status pd_run_pipeline(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H,
                           size_t pitch, const pd_road_model* model, const pd_params* p,
                           const pd_outputs* out, pd_stage_times* times) {
@@ -836,12 +855,22 @@ pd_status pd_run_pipeline(pd_ctx* ctx, const uint8_t* left, const uint8_t* right
   PD_REQUIRE(p->slic_iters >= 0 && p->slic_iters <= 1000, "slic_iters out of range");
   PD_REQUIRE(p->threshold_mode == 0 || p->threshold_mode == 1, "threshold_mode must be 0 or 1");
   PD_REQUIRE(isfinite(p->delta_dt) && isfinite(p->delta_pd), "non-finite delta");
+  const bool ccl = out->components != nullptr;
+  const int conn = out->connectivity == 0 ? 8 : out->connectivity;
+  if (ccl) {
+    PD_REQUIRE(out->n_comps != nullptr, "pd_outputs.components needs n_comps");
+    PD_REQUIRE(conn == 4 || conn == 8, "connectivity %d must be 4 or 8", conn);
+    PD_REQUIRE(out->max_comps >= 0 && (out->max_comps == 0 || out->comps != nullptr),
+               "max_comps %d needs a component buffer of that size", out->max_comps);
+  }
+  const int max_comps = out->max_comps < W * H ? out->max_comps : W * H;
   int nx, ny;
   slic_grid(W, H, p->slic_K, &nx, &ny);
   size_t need = sgm_scratch_bytes(W, H, p->D, p->paths);
   size_t other = transform_scratch_bytes(W, H);
   if (slic_scratch_bytes(nx * ny) > other) other = slic_scratch_bytes(nx * ny);
   if (threshold_scratch_bytes() > other) other = threshold_scratch_bytes();
+  if (ccl && ccl_scratch_bytes(W, H, max_comps) > other) other = ccl_scratch_bytes(W, H, max_comps);
   if (other > need) need = other;
   PD_TRY(ensure_ws(ctx, need));
   if (times && !ctx->ev[0])
@@ -864,6 +893,9 @@ pd_status pd_run_pipeline(pd_ctx* ctx, const uint8_t* left, const uint8_t* right
   launch_threshold(s, out->D2, out->D1, out->D3, W, H, p->delta_pd, p->threshold_mode, out->mask,
                    out->thresholds, nullptr, ctx->ws);
   count_launches(ctx, 3);
+  if (ccl)
+    count_launches(ctx, launch_ccl(s, out->mask, out->labels, W, H, conn, out->components,
+                                   out->comps, max_comps, out->n_comps, ctx->ws));
   mark(ctx, rec, 6);
   if (times) cudaEventRecord(ctx->ev[4], s);
   PD_TRY(launched(ctx, "pd_run_pipeline"));

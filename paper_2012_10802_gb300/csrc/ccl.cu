@@ -1,0 +1,269 @@
+// Sec. II-E: connected components of the pothole mask ("different potholes are labeled using
+// connect component labeling"), their statistics, and the fake-pothole rule of Sec. III-B
+// (detections at a corner of the image or made of a single superpixel are fake).
+//
+// Labelling is union-find over the pixel grid: every mask pixel starts as its own root, each
+// pixel merges with its already-visited neighbours (left, up, and the two upper diagonals for
+// 8-connectivity) by attaching the larger root under the smaller one with atomicMin, and a
+// final pass points every pixel at its root.  The root of a component is therefore its smallest
+// raster index.  Components are numbered in the raster order of their roots (block counts, one
+// scan, per-block ranks), so the numbering does not depend on thread timing.  Every find and
+// merge loop has an iteration limit; exceeding it sets an error flag (reported as a component
+// count of -1) instead of looping on.
+#include <limits.h>
+
+#include "common.cuh"
+
+namespace pd {
+
+namespace {
+
+constexpr int kCclThreads = 1024;
+static_assert(sizeof(pd_component) == 56, "pd_component layout");
+constexpr int kLoopCap = 1 << 22;
+
+__device__ __forceinline__ int find_root(const int32_t* L, int x, int* err) {
+  for (int it = 0; it < kLoopCap; ++it) {
+    const int y = __ldcg(L + x);  // parents change under other threads: read through L2
+    if (y == x) return x;
+    x = y;
+  }
+  atomicExch(err, 1);
+  return x;
+}
+
+__device__ __forceinline__ void merge(int32_t* L, int a, int b, int* err) {
+  for (int it = 0; it < kLoopCap; ++it) {
+    a = find_root(L, a, err);
+    b = find_root(L, b, err);
+    if (a == b) return;
+    if (a > b) {
+      const int t = a;
+      a = b;
+      b = t;
+    }
+    const int old = atomicMin(L + b, a);  // attach root b under the smaller root a
+    if (old == b) return;
+    b = old;  // b stopped being a root meanwhile: retry from its new parent
+  }
+  atomicExch(err, 1);
+}
+
+__global__ void k_ccl_init(const uint8_t* __restrict__ mask, int n, int32_t* __restrict__ L) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) L[p] = mask[p] ? p : -1;
+}
+
+__global__ void k_ccl_merge(const uint8_t* __restrict__ mask, int W, int H, int conn,
+                            int32_t* L, int* err) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= W * H || !mask[p]) return;
+  const int u = p % W, v = p / W;
+  if (u > 0 && mask[p - 1]) merge(L, p, p - 1, err);
+  if (v > 0) {
+    const int q = p - W;
+    if (mask[q]) merge(L, p, q, err);
+    if (conn == 8) {
+      if (u > 0 && mask[q - 1]) merge(L, p, q - 1, err);
+      if (u < W - 1 && mask[q + 1]) merge(L, p, q + 1, err);
+    }
+  }
+}
+
+__global__ void k_ccl_flatten(int32_t* L, int n, int* err) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n && __ldcg(L + p) >= 0) L[p] = find_root(L, p, err);
+}
+
+// Roots per block of kCclThreads pixels.
+__global__ void __launch_bounds__(kCclThreads) k_ccl_count(const int32_t* __restrict__ L, int n,
+                                                           int* __restrict__ counts) {
+  const int p = blockIdx.x * kCclThreads + threadIdx.x;
+  const int c = __syncthreads_count(p < n && L[p] == p);
+  if (threadIdx.x == 0) counts[blockIdx.x] = c;
+}
+
+// Exclusive scan of the block counts in one block; total number of components in *total.
+__global__ void __launch_bounds__(kCclThreads) k_ccl_scan(const int* __restrict__ counts, int nb,
+                                                          int* __restrict__ offsets,
+                                                          int* __restrict__ total) {
+  __shared__ int warp_sums[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int base = 0; base < nb; base += kCclThreads) {
+    const int i = base + threadIdx.x;
+    const int x = i < nb ? counts[i] : 0;
+    int incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_sums[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+      int ws = warp_sums[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, ws, o);
+        if (lane >= o) ws += y;
+      }
+      warp_sums[lane] = ws;  // inclusive over warps
+    }
+    __syncthreads();
+    const int before = (w > 0 ? warp_sums[w - 1] : 0) + incl - x;
+    if (i < nb) offsets[i] = carry + before;
+    __syncthreads();
+    if (threadIdx.x == kCclThreads - 1) carry += warp_sums[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+// Component number of every root (raster order of roots) and the root of every component.
+__global__ void __launch_bounds__(kCclThreads) k_ccl_ids(const int32_t* __restrict__ L, int n,
+                                                         const int* __restrict__ offsets,
+                                                         int32_t* __restrict__ cid,
+                                                         int32_t* __restrict__ root_of,
+                                                         int max_comps) {
+  __shared__ int warp_cnt[32];
+  const int p = blockIdx.x * kCclThreads + threadIdx.x;
+  const bool root = p < n && L[p] == p;
+  const unsigned bal = __ballot_sync(0xffffffffu, root);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) warp_cnt[w] = __popc(bal);
+  __syncthreads();
+  if (root) {
+    int r = __popc(bal & ((1u << lane) - 1u));
+    for (int k = 0; k < w; ++k) r += warp_cnt[k];
+    const int id = offsets[blockIdx.x] + r;
+    cid[p] = id;
+    if (id < max_comps) root_of[id] = p;
+  }
+}
+
+struct CompAcc {
+  int count, umin, vmin, umax, vmax, sp_first, multi, pad;
+  unsigned long long sum_u, sum_v;
+};
+
+__global__ void k_ccl_acc_init(CompAcc* acc, int max_comps) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= max_comps) return;
+  CompAcc a;
+  a.count = 0;
+  a.umin = INT_MAX;
+  a.vmin = INT_MAX;
+  a.umax = -1;
+  a.vmax = -1;
+  a.sp_first = INT_MIN;
+  a.multi = 0;
+  a.pad = 0;
+  a.sum_u = 0;
+  a.sum_v = 0;
+  acc[k] = a;
+}
+
+// Per mask pixel: the output label (component number) and its share of the statistics.
+__global__ void k_ccl_stats(const int32_t* __restrict__ L, const int32_t* __restrict__ cid,
+                            const int32_t* __restrict__ sp, int W, int H,
+                            int32_t* __restrict__ labels, CompAcc* acc, int max_comps) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= W * H) return;
+  const int r = L[p];
+  if (r < 0) {
+    labels[p] = -1;
+    return;
+  }
+  const int k = cid[r];
+  labels[p] = k;
+  if (k >= max_comps) return;
+  const int u = p % W, v = p / W;
+  CompAcc* a = acc + k;
+  atomicAdd(&a->count, 1);
+  atomicMin(&a->umin, u);
+  atomicMin(&a->vmin, v);
+  atomicMax(&a->umax, u);
+  atomicMax(&a->vmax, v);
+  atomicAdd(&a->sum_u, (unsigned long long)u);
+  atomicAdd(&a->sum_v, (unsigned long long)v);
+  const int s = sp[p];
+  const int old = atomicCAS(&a->sp_first, INT_MIN, s);
+  if (old != INT_MIN && old != s) a->multi = 1;
+}
+
+// Statistics and the fake-pothole rule: the centroid lies in a corner cell of the image split
+// 8 x 8 (compared exactly in integers), or every pixel carries the same superpixel label.
+__global__ void k_ccl_finalize(const CompAcc* __restrict__ acc, const int32_t* __restrict__ root_of,
+                               const int* __restrict__ total, const int* __restrict__ err, int W,
+                               int H, int max_comps, pd_component* __restrict__ comps,
+                               int* __restrict__ n_comps) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = *total;
+  if (k == 0) *n_comps = *err ? -1 : n;
+  if (k >= n || k >= max_comps) return;
+  const CompAcc a = acc[k];
+  pd_component c;
+  c.label = root_of[k];
+  c.count = a.count;
+  c.umin = a.umin;
+  c.vmin = a.vmin;
+  c.umax = a.umax;
+  c.vmax = a.vmax;
+  c.sum_u = (int64_t)a.sum_u;
+  c.sum_v = (int64_t)a.sum_v;
+  const int64_t cnt = a.count;
+  const bool left = 8 * c.sum_u < (int64_t)W * cnt, right = 8 * c.sum_u >= (int64_t)7 * W * cnt;
+  const bool top = 8 * c.sum_v < (int64_t)H * cnt, bottom = 8 * c.sum_v >= (int64_t)7 * H * cnt;
+  c.superpixels = a.multi ? 2 : 1;
+  c.corner = (left || right) && (top || bottom);
+  c.single = !a.multi;
+  c.fake = c.corner || c.single;
+  comps[k] = c;
+}
+
+}  // namespace
+
+size_t ccl_scratch_bytes(int W, int H, int max_comps) {
+  const size_t n = (size_t)W * H, nb = (n + kCclThreads - 1) / kCclThreads;
+  size_t acc = 0;
+  carve_size<int32_t>(acc, n);         // L
+  carve_size<int32_t>(acc, n);         // cid
+  carve_size<int>(acc, nb);            // counts
+  carve_size<int>(acc, nb);            // offsets
+  carve_size<int>(acc, 2);             // total, err
+  carve_size<int32_t>(acc, max_comps); // root_of
+  carve_size<CompAcc>(acc, max_comps);
+  return acc;
+}
+
+int launch_ccl(cudaStream_t s, const uint8_t* mask, const int32_t* sp, int W, int H, int conn,
+               int32_t* labels, pd_component* comps, int max_comps, int* n_comps, void* scratch) {
+  const int n = W * H, nb = (n + kCclThreads - 1) / kCclThreads;
+  Carve c(scratch);
+  int32_t* L = c.take<int32_t>(n);
+  int32_t* cid = c.take<int32_t>(n);
+  int* counts = c.take<int>(nb);
+  int* offsets = c.take<int>(nb);
+  int* flags = c.take<int>(2);  // total, err
+  int32_t* root_of = c.take<int32_t>(max_comps);
+  CompAcc* acc = c.take<CompAcc>(max_comps);
+  const int T = 256, G = (n + T - 1) / T;
+  cudaMemsetAsync(flags, 0, 2 * sizeof(int), s);
+  k_ccl_init<<<G, T, 0, s>>>(mask, n, L);
+  k_ccl_merge<<<G, T, 0, s>>>(mask, W, H, conn, L, flags + 1);
+  k_ccl_flatten<<<G, T, 0, s>>>(L, n, flags + 1);
+  k_ccl_count<<<nb, kCclThreads, 0, s>>>(L, n, counts);
+  k_ccl_scan<<<1, kCclThreads, 0, s>>>(counts, nb, offsets, flags);
+  k_ccl_ids<<<nb, kCclThreads, 0, s>>>(L, n, offsets, cid, root_of, max_comps);
+  const int GK = (max_comps + T - 1) / T;
+  k_ccl_acc_init<<<GK > 0 ? GK : 1, T, 0, s>>>(acc, max_comps);
+  k_ccl_stats<<<G, T, 0, s>>>(L, cid, sp, W, H, labels, acc, max_comps);
+  k_ccl_finalize<<<GK > 0 ? GK : 1, T, 0, s>>>(acc, root_of, flags, flags + 1, W, H, max_comps,
+                                               comps, n_comps);
+  return 10;
+}
+
+}  // namespace pd

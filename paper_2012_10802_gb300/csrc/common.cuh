@@ -133,6 +133,11 @@ void launch_lr_band(cudaStream_t s, const int16_t* d_int, const float* dsub, con
                     const int32_t* kappa, int W, int H, int D, const BandArgs& band, int lr_tol,
                     float* D1);
 
+// Connected components (ccl.cu); returns the number of kernels launched.
+size_t ccl_scratch_bytes(int W, int H, int max_comps);
+int launch_ccl(cudaStream_t s, const uint8_t* mask, const int32_t* sp, int W, int H, int conn,
+               int32_t* labels, pd_component* comps, int max_comps, int* n_comps, void* scratch);
+
 // The band network (cnn.cu).
 bool cnn_fits(const pd_cnn* net, int B, int Hd, int Wd);
 const float* cnn_forward_enqueue(cudaStream_t s, pd_cnn* net, const void* x, int Hd, int Wd);

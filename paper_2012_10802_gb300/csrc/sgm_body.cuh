@@ -202,10 +202,11 @@ __device__ __forceinline__ LineWalk line_walk(int dx, int dy, int W, int H, int 
   return w;
 }
 
-// The window of pixel (u, v) (see BandArgs).
+// The window of pixel (u, v) (see BandArgs).  tile_lo may point to global or shared memory
+// (a generic load).
 __device__ __forceinline__ void band_window(const BandArgs& b, int u, int v, int D, int& lo,
                                             int& hi) {
-  const int t = __ldg(b.tile_lo + (v >> 4) * b.tw + (u >> 4));
+  const int t = b.tile_lo[(v >> 4) * b.tw + (u >> 4)];
   lo = t < 0 ? 0 : min(t, D - 1);
   hi = t < 0 ? D : min(lo + b.width, D);
 }
@@ -216,22 +217,13 @@ __device__ __forceinline__ uint32_t group_in_mask(int g, int lo, int hi) {
   return ((1u << b) - 1u) & ~((1u << a) - 1u);
 }
 
-// "Outside the window" marker for the u16 halves of word j: 0x4000 added to a value below 0x4000
-// keeps it above every in-window value and below 0x8000, so later additions cannot wrap.
-__device__ __forceinline__ uint32_t out_marks(uint32_t in16, int j) {
-  const uint32_t out = ~in16;
-  return (((out >> j) & 1u) * 0x4000u) | (((out >> (8 + j)) & 1u) * 0x40000000u);
-}
-
 // The lines first .. first + 32/G - 1 of direction (dx, dy), walked by the calling warp (all 32
 // lanes call it; `warp` selects the warp's part of the block's cost ring).  L goes to dst_vol.
-// With BAND, every pixel searches only its tile's window (L = infinity elsewhere, represented by
-// the 0x4000 marker); lanes whose 16 disparities all lie outside skip their loads and stores.
-template <int G, bool BAND = false>
+template <int G>
 __device__ __forceinline__ void agg_warp(const uint8_t* __restrict__ cost,
                                          uint8_t* __restrict__ dst_vol, int W, int H, int D,
                                          int dx, int dy, uint32_t P1x2, uint32_t K21x2, int first,
-                                         int warp, BandArgs band = BandArgs{nullptr, 0, 0}) {
+                                         int warp) {
   constexpr int LPW = 32 / G;  // lines per warp
   const int nlines = dy == 0 ? H : (dx == 0 ? W : W + H - 1);
   const int lane = threadIdx.x & 31;
@@ -258,35 +250,9 @@ __device__ __forceinline__ void agg_warp(const uint8_t* __restrict__ cost,
   uint4* ring = s_ring + (size_t)warp * kStages * 32 + lane;
   const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
   long long pf_off = lw.off0;  // offset of the step being prefetched
-  // band state: pixel of the prefetched step and of the current step, each with the tile whose
-  // window was looked up last
-  int pu = lw.u0, pv = lw.v0, cu = lw.u0, cv = lw.v0;
-  int p_tile = -1, c_tile = -1;
-  bool p_act = true;
-  uint32_t c_in = 0xffffu;
-  uint32_t M[8];
-#pragma unroll
-  for (int j = 0; j < 8; ++j) M[j] = 0;
-  auto prefetch_active = [&](bool in) -> bool {
-    if constexpr (BAND) {
-      if (in) {
-        const int t = (pv >> 4) * band.tw + (pu >> 4);
-        if (t != p_tile) {
-          int lo, hi;
-          band_window(band, pu, pv, D, lo, hi);
-          p_act = 16 * g < hi && 16 * g + 16 > lo;
-          p_tile = t;
-        }
-        in = p_act;
-      }
-      pu += dx;
-      pv += dy;
-    }
-    return in;
-  };
 #pragma unroll
   for (int k = 0; k < kStages - 1; ++k) {
-    const bool in = prefetch_active(k >= lw.s_first && k <= lw.s_last);
+    const bool in = k >= lw.s_first && k <= lw.s_last;
     cp_async16(ring_s + k * 32 * 16, csrc + (in ? pf_off : 0), in ? 16u : 0u);
     cp_async_commit();
     pf_off += lw.delta;
@@ -303,7 +269,7 @@ __device__ __forceinline__ void agg_warp(const uint8_t* __restrict__ cost,
       const uint32_t raw[4] = {rv.x, rv.y, rv.z, rv.w};
       {
         const int sp = s + kStages - 1;
-        const bool in = prefetch_active(sp >= lw.s_first && sp <= lw.s_last);
+        const bool in = sp >= lw.s_first && sp <= lw.s_last;
         cp_async16(ring_s + ((k + kStages - 1) % kStages) * 32 * 16, csrc + (in ? pf_off : 0),
                    in ? 16u : 0u);
         cp_async_commit();
@@ -333,23 +299,6 @@ __device__ __forceinline__ void agg_warp(const uint8_t* __restrict__ cost,
         // carry crosses between the halves
         Lw[j] = t + c - mp;
       }
-      if constexpr (BAND) {
-        if (act) {
-          const int tl = (cv >> 4) * band.tw + (cu >> 4);
-          if (tl != c_tile) {
-            int lo, hi;
-            band_window(band, cu, cv, D, lo, hi);
-            c_in = group_in_mask(g, lo, hi);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) M[j] = out_marks(c_in, j);
-            c_tile = tl;
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < 8; ++j) Lw[j] |= M[j];
-        cu += dx;
-        cv += dy;
-      }
       uint32_t m = __vimin3_u16x2(__vimin3_u16x2(Lw[0], Lw[1], Lw[2]),
                                   __vimin3_u16x2(Lw[3], Lw[4], Lw[5]), __vminu2(Lw[6], Lw[7]));
       m = __vminu2(m, __byte_perm(m, m, 0x1032));  // both halves = min of the two halves
@@ -361,7 +310,7 @@ __device__ __forceinline__ void agg_warp(const uint8_t* __restrict__ cost,
         w.y = __byte_perm(Lw[2], Lw[3], 0x6420);
         w.z = __byte_perm(Lw[4], Lw[5], 0x6420);
         w.w = __byte_perm(Lw[6], Lw[7], 0x6420);
-        if (!BAND || c_in != 0) __stcs(reinterpret_cast<uint4*>(dst + st_off), w);
+        __stcs(reinterpret_cast<uint4*>(dst + st_off), w);
 #pragma unroll
         for (int j = 0; j < 8; ++j) N[j] = Lw[j];
         mp = m;

@@ -258,6 +258,17 @@ def test_pipeline_parity(orc, B, ctx, W, H, D, paths):
     assert agree.mean() >= 0.999
     assert np.array_equal(host(t["mask"])[agree], ref["mask"][agree])
     assert times.total_ms > 0
+    # Sec. II-E components of the mask, against the oracle's labelling of its own mask
+    recs, n = B.component_records(outs)
+    lab_ref, n_ref = orc.ccl(ref["mask"].astype(np.uint8), 8)
+    if agree.all() and np.array_equal(host(t["mask"]), ref["mask"]):
+        comps_ref = orc.components(lab_ref, ref["labels"], n_ref)
+        assert n == n_ref
+        got = np.stack([recs[f].astype(np.int64) for f in orc.COMPONENT_FIELDS], axis=1)
+        assert np.array_equal(got, comps_ref)
+        expect = np.where(lab_ref >= 0, np.searchsorted(comps_ref[:, 0], lab_ref), -1)
+        assert np.array_equal(host(t["components"]), expect)
+    assert n >= 0   # -1 would mean the union-find hit its iteration limit
 
 
 # ---------------------------------------------------------------------- errors and edges
