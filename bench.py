@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-pair mixed batch")
     ap.add_argument("--no-band", action="store_true", help="skip the learned-band comparison")
+    ap.add_argument("--band-size", default=None,
+                    help="WxH: only time pd_sgm_band on a road of that size with every tile "
+                         "banded around its full-range median (for profiling)")
     ap.add_argument("--size", default=None,
                     help="WxH of a smaller road for profiling captures (not a benchmark line)")
     return ap.parse_args()
@@ -235,6 +238,38 @@ def bench_batch(B, torch, synth, n_pairs=64, steps=5, seq_steps=2):
             "identical_to_sequential": bool(same)}
 
 
+def band_only(B, torch, synth, size, steps, warmup):
+    """pd_sgm_band at W x H, D = 128, 8 paths, every tile banded with a 17-disparity window around
+    its full-range median (the learned band's common case); prints one JSON line."""
+    W, H = (int(x) for x in size.lower().split("x"))
+    D = 128
+    ctx = B.Context(torch.cuda.current_device())
+    sc = synth.road_scaled(W, H, 20000)
+    left, right = synth.render_torch(sc, "cuda")
+    model = B.RoadModel.make(*synth.true_model(sc))
+    p = B.default_params(D=D)
+    kap, d_full, D1_full = B.pd_sgm(ctx, left, right, model, p)
+    th, tw = (H + 15) // 16, (W + 15) // 16
+    pad = torch.nn.functional.pad(d_full.float(), (0, tw * 16 - W, 0, th * 16 - H), value=float("nan"))
+    med = torch.nanmedian(pad.reshape(th, 16, tw, 16).permute(0, 2, 1, 3).reshape(th, tw, 256), 2)
+    tile_lo = torch.clamp(torch.round(med.values) - 8, 0, D - 17).to(torch.int16)
+    d_int, D1 = torch.empty_like(d_full), torch.empty_like(D1_full)
+    for _ in range(warmup):
+        B.pd_sgm_band(ctx, left, right, model, p, tile_lo, 17, kap, d_int, D1)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        B.pd_sgm_band(ctx, left, right, model, p, tile_lo, 17, kap, d_int, D1)
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    ctx.close()
+    print(json.dumps({"workload": "pd_sgm_band %dx%d D=128 8 paths, every tile banded" % (W, H),
+                      "ms_median": statistics.median(ms), "steps": steps}))
+
+
 def bench_band(B, torch, synth, steps=10, n_eval=4):
     """The learned band at 1920x1080, D = 128, 8 paths: the band network (committed weights,
     trained on 2000 synthetic pairs by the library's own kernels) picks a 17-disparity window per
@@ -324,6 +359,8 @@ def main():
     from paper_2012_10802_gb300 import synth
 
     torch.cuda.set_device(local)
+    if args.band_size:
+        return band_only(B, torch, synth, args.band_size, args.steps, max(args.warmup, 3))
     dist = None
     if world > 1:
         import torch.distributed as dist

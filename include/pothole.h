@@ -390,7 +390,9 @@ pd_status pd_band_labels(pd_ctx* ctx, const int16_t* d_int, const float* D1, int
                          float* targets);
 
 /* Windows from the network output: tiles with out1 >= ln 9 (confidence >= 0.9) start at
- * rint(16 out0) - band_width / 2 moved into [0, D - band_width]; the others get -1 (full range).
+ * rint(16 out0) - band_width / 2 moved into [0, D - band_width]; the others get -1 (full range),
+ * except that an unconfident tile of the left border columns tx < t0 = ceil((D - 1) / 16), where
+ * the full-range search has no valid pixel, takes the window of tile (ty, t0).
  * cnn_out: float [tiles_h][tiles_w][2]; tile_lo: int16 [tiles_h][tiles_w] (device). */
 pd_status pd_band_tiles(pd_ctx* ctx, const float* cnn_out, int tiles_h, int tiles_w, int D,
                         int band_width, int16_t* tile_lo);

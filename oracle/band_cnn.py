@@ -232,8 +232,15 @@ def labels(d_int, D1, tiles_h, tiles_w):
 def tile_windows(out, D, band=BAND):
     """out [Ho][Wo][2] (float32) -> per-tile window start (int16), -1 for full range: confident
     tiles (logit >= ln 9 in float32) start at rint(CENTRE_SCALE * o0) - 8 (float32 arithmetic,
-    ties to even), moved inside [0, D - band]."""
+    ties to even), moved inside [0, D - band].  Unconfident tiles of the left border columns
+    tx < t0 = ceil((D - 1) / 16), where the full-range search has no valid pixel and so no label
+    exists, take the window of tile (ty, t0) when that tile is confident."""
     o = np.asarray(out, np.float32)
     c = np.rint(o[..., 0] * np.float32(CENTRE_SCALE))
     lo = np.clip(c - (band // 2), 0, max(D - band, 0)).astype(np.int16)
-    return np.where(o[..., 1] >= CONF_LOGIT, lo, np.int16(-1)).astype(np.int16)
+    win = np.where(o[..., 1] >= CONF_LOGIT, lo, np.int16(-1)).astype(np.int16)
+    t0 = (D - 1 + 15) // 16
+    if t0 < win.shape[1]:
+        for tx in range(t0):
+            win[:, tx] = np.where(win[:, tx] < 0, win[:, t0], win[:, tx])
+    return win

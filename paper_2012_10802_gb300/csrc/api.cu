@@ -763,7 +763,7 @@ pd_status pd_sgm_learned(pd_ctx* ctx, pd_cnn* net, const uint8_t* left, const ui
                (double)params->delta_pt, kap);
   launch_band_input(s, left, right, W, H, pitch, kap, x);
   const float* out = cnn_forward_enqueue(s, net, x, Hd, Wd);
-  launch_band_tiles(s, out, th * tw, params->D, band_width, tl);
+  launch_band_tiles(s, out, th, tw, params->D, band_width, tl);
   count_launches(ctx, 11);
   BandArgs band{tl, tw, band_width};
   return sgm_band_enqueue(ctx, left, right, W, H, pitch, model, params, band, kap, d_int, D1,

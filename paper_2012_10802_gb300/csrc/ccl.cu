@@ -6,7 +6,9 @@
 // pixel merges with its already-visited neighbours (left, up, and the two upper diagonals for
 // 8-connectivity) by attaching the larger root under the smaller one with atomicMin, and a
 // final pass points every pixel at its root.  The root of a component is therefore its smallest
-// raster index.  Components are numbered in the raster order of their roots (block counts, one
+// raster index.  The merges run first inside 16 x 16 tiles in shared memory and then only
+// across tile borders in global memory, so a large pothole does not funnel every pixel's atomic
+// into one root.  Components are numbered in the raster order of their roots (block counts, one
 // scan, per-block ranks), so the numbering does not depend on thread timing.  Every find and
 // merge loop has an iteration limit; exceeding it sets an error flag (reported as a component
 // count of -1) instead of looping on.
@@ -49,44 +51,131 @@ __device__ __forceinline__ void merge(int32_t* L, int a, int b, int* err) {
   atomicExch(err, 1);
 }
 
-__global__ void k_ccl_init(const uint8_t* __restrict__ mask, int n, int32_t* __restrict__ L) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < n) L[p] = mask[p] ? p : -1;
+// Labels inside one 16 x 16 tile, in shared memory: the same union-find on tile-local indices
+// (local raster order within a tile agrees with the global raster order of its pixels), then
+// every mask pixel gets the global raster index of its tile-local root.  Block 0 also clears the
+// flags (component total and error) for the later kernels.
+constexpr int kTile = 16;
+
+__device__ __forceinline__ int find_local(const int* s, int x) {
+  const volatile int* vs = s;  // parents change under other threads of the block
+  for (int it = 0; it < kTile * kTile; ++it) {
+    const int y = vs[x];
+    if (y == x) return x;
+    x = y;
+  }
+  return x;
 }
 
-__global__ void k_ccl_merge(const uint8_t* __restrict__ mask, int W, int H, int conn,
-                            int32_t* L, int* err) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= W * H || !mask[p]) return;
-  const int u = p % W, v = p / W;
-  if (u > 0 && mask[p - 1]) merge(L, p, p - 1, err);
-  if (v > 0) {
-    const int q = p - W;
-    if (mask[q]) merge(L, p, q, err);
-    if (conn == 8) {
-      if (u > 0 && mask[q - 1]) merge(L, p, q - 1, err);
-      if (u < W - 1 && mask[q + 1]) merge(L, p, q + 1, err);
+__device__ __forceinline__ void merge_local(int* s, int a, int b) {
+  for (int it = 0; it < 4 * kTile * kTile; ++it) {
+    a = find_local(s, a);
+    b = find_local(s, b);
+    if (a == b) return;
+    if (a > b) {
+      const int t = a;
+      a = b;
+      b = t;
     }
+    const int old = atomicMin(s + b, a);
+    if (old == b) return;
+    b = old;
   }
 }
 
-__global__ void k_ccl_flatten(int32_t* L, int n, int* err) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < n && __ldcg(L + p) >= 0) L[p] = find_root(L, p, err);
+__global__ void __launch_bounds__(kTile * kTile) k_ccl_local(const uint8_t* __restrict__ mask,
+                                                             int W, int H, int conn,
+                                                             int32_t* __restrict__ L, int* flags) {
+  __shared__ int s[kTile * kTile];
+  const int tx = threadIdx.x % kTile, ty = threadIdx.x / kTile;
+  const int u = blockIdx.x * kTile + tx, v = blockIdx.y * kTile + ty;
+  const bool in = u < W && v < H;
+  const bool m = in && mask[(size_t)v * W + u];
+  const int me = threadIdx.x;
+  s[me] = m ? me : -1;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < 2) flags[threadIdx.x] = 0;
+  __syncthreads();
+  if (m) {
+    if (tx > 0 && s[me - 1] >= 0) merge_local(s, me, me - 1);
+    if (ty > 0) {
+      if (s[me - kTile] >= 0) merge_local(s, me, me - kTile);
+      if (conn == 8) {
+        if (tx > 0 && s[me - kTile - 1] >= 0) merge_local(s, me, me - kTile - 1);
+        if (tx < kTile - 1 && s[me - kTile + 1] >= 0) merge_local(s, me, me - kTile + 1);
+      }
+    }
+  }
+  __syncthreads();
+  if (!in) return;
+  int root = -1;
+  if (m) {
+    const int r = find_local(s, me);
+    root = (blockIdx.y * kTile + r / kTile) * W + blockIdx.x * kTile + r % kTile;
+  }
+  L[(size_t)v * W + u] = root;
 }
 
-// Roots per block of kCclThreads pixels.
-__global__ void __launch_bounds__(kCclThreads) k_ccl_count(const int32_t* __restrict__ L, int n,
-                                                           int* __restrict__ counts) {
+// Unions across tile borders: each mask pixel with an earlier neighbour (left, up, up-left,
+// up-right) in another tile merges with it through the global union-find.
+__global__ void __launch_bounds__(kTile * kTile) k_ccl_border(const uint8_t* __restrict__ mask,
+                                                              int W, int H, int conn, int32_t* L,
+                                                              int* err) {
+  const int tx = threadIdx.x % kTile, ty = threadIdx.x / kTile;
+  if (tx != 0 && ty != 0 && tx != kTile - 1) return;  // interior pixels were merged locally
+  const int u = blockIdx.x * kTile + tx, v = blockIdx.y * kTile + ty;
+  if (u >= W || v >= H) return;
+  const int p = v * W + u;
+  if (!mask[p]) return;
+  if (tx == 0 && u > 0 && mask[p - 1]) merge(L, p, p - 1, err);
+  if (ty == 0 && v > 0 && mask[p - W]) merge(L, p, p - W, err);
+  if (conn == 8 && v > 0) {
+    if ((tx == 0 || ty == 0) && u > 0 && mask[p - W - 1]) merge(L, p, p - W - 1, err);
+    if ((ty == 0 || tx == kTile - 1) && u < W - 1 && mask[p - W + 1]) merge(L, p, p - W + 1, err);
+  }
+}
+
+// Every mask pixel points at its root; roots are counted per block of kCclThreads pixels.
+__global__ void __launch_bounds__(kCclThreads) k_ccl_flatten_count(int32_t* L, int n, int* err,
+                                                                   int* __restrict__ counts) {
   const int p = blockIdx.x * kCclThreads + threadIdx.x;
-  const int c = __syncthreads_count(p < n && L[p] == p);
+  bool root = false;
+  if (p < n) {
+    const int r = __ldcg(L + p);
+    if (r >= 0) {
+      root = r == p;
+      if (!root) L[p] = find_root(L, p, err);
+    }
+  }
+  const int c = __syncthreads_count(root);
   if (threadIdx.x == 0) counts[blockIdx.x] = c;
 }
 
 // Exclusive scan of the block counts in one block; total number of components in *total.
+struct CompAcc {
+  int count, umin, vmin, umax, vmax, sp_first, multi, pad;
+  unsigned long long sum_u, sum_v;
+};
+
+__device__ void acc_init_one(CompAcc* out) {
+  CompAcc a;
+  a.count = 0;
+  a.umin = INT_MAX;
+  a.vmin = INT_MAX;
+  a.umax = -1;
+  a.vmax = -1;
+  a.sp_first = INT_MIN;
+  a.multi = 0;
+  a.pad = 0;
+  a.sum_u = 0;
+  a.sum_v = 0;
+  *out = a;
+}
+
 __global__ void __launch_bounds__(kCclThreads) k_ccl_scan(const int* __restrict__ counts, int nb,
                                                           int* __restrict__ offsets,
-                                                          int* __restrict__ total) {
+                                                          int* __restrict__ total, CompAcc* acc,
+                                                          int max_comps) {
+  for (int k = threadIdx.x; k < max_comps; k += kCclThreads) acc_init_one(acc + k);
   __shared__ int warp_sums[32];
   __shared__ int carry;
   if (threadIdx.x == 0) carry = 0;
@@ -142,28 +231,6 @@ __global__ void __launch_bounds__(kCclThreads) k_ccl_ids(const int32_t* __restri
     cid[p] = id;
     if (id < max_comps) root_of[id] = p;
   }
-}
-
-struct CompAcc {
-  int count, umin, vmin, umax, vmax, sp_first, multi, pad;
-  unsigned long long sum_u, sum_v;
-};
-
-__global__ void k_ccl_acc_init(CompAcc* acc, int max_comps) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= max_comps) return;
-  CompAcc a;
-  a.count = 0;
-  a.umin = INT_MAX;
-  a.vmin = INT_MAX;
-  a.umax = -1;
-  a.vmax = -1;
-  a.sp_first = INT_MIN;
-  a.multi = 0;
-  a.pad = 0;
-  a.sum_u = 0;
-  a.sum_v = 0;
-  acc[k] = a;
 }
 
 // Per mask pixel: the output label (component number) and its share of the statistics.
@@ -251,19 +318,17 @@ int launch_ccl(cudaStream_t s, const uint8_t* mask, const int32_t* sp, int W, in
   int32_t* root_of = c.take<int32_t>(max_comps);
   CompAcc* acc = c.take<CompAcc>(max_comps);
   const int T = 256, G = (n + T - 1) / T;
-  cudaMemsetAsync(flags, 0, 2 * sizeof(int), s);
-  k_ccl_init<<<G, T, 0, s>>>(mask, n, L);
-  k_ccl_merge<<<G, T, 0, s>>>(mask, W, H, conn, L, flags + 1);
-  k_ccl_flatten<<<G, T, 0, s>>>(L, n, flags + 1);
-  k_ccl_count<<<nb, kCclThreads, 0, s>>>(L, n, counts);
-  k_ccl_scan<<<1, kCclThreads, 0, s>>>(counts, nb, offsets, flags);
+  const dim3 tiles((W + kTile - 1) / kTile, (H + kTile - 1) / kTile);
+  k_ccl_local<<<tiles, kTile * kTile, 0, s>>>(mask, W, H, conn, L, flags);
+  k_ccl_border<<<tiles, kTile * kTile, 0, s>>>(mask, W, H, conn, L, flags + 1);
+  k_ccl_flatten_count<<<nb, kCclThreads, 0, s>>>(L, n, flags + 1, counts);
+  k_ccl_scan<<<1, kCclThreads, 0, s>>>(counts, nb, offsets, flags, acc, max_comps);
   k_ccl_ids<<<nb, kCclThreads, 0, s>>>(L, n, offsets, cid, root_of, max_comps);
-  const int GK = (max_comps + T - 1) / T;
-  k_ccl_acc_init<<<GK > 0 ? GK : 1, T, 0, s>>>(acc, max_comps);
   k_ccl_stats<<<G, T, 0, s>>>(L, cid, sp, W, H, labels, acc, max_comps);
+  const int GK = (max_comps + T - 1) / T;
   k_ccl_finalize<<<GK > 0 ? GK : 1, T, 0, s>>>(acc, root_of, flags, flags + 1, W, H, max_comps,
                                                comps, n_comps);
-  return 10;
+  return 7;
 }
 
 }  // namespace pd

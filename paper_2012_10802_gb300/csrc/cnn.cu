@@ -484,17 +484,25 @@ __global__ void __launch_bounds__(256) k_band_labels(const int16_t* __restrict__
   }
 }
 
-// Confident tiles (logit >= ln 9 in float) start at rint(16 o0) - band/2 moved into [0, D - band];
-// the others search the full range (-1).
-__global__ void k_band_tiles(const float* __restrict__ out, int n, int D, int band,
+// Window of one tile from the network output: confident tiles (logit >= ln 9 in float) start at
+// rint(16 o0) - band/2 moved into [0, D - band]; the others search the full range (-1).
+__device__ __forceinline__ int16_t tile_window(const float* o, int D, int band) {
+  const float c = rintf(o[0] * 16.0f) - (float)(band / 2);
+  const float lo = fminf(fmaxf(c, 0.0f), (float)max(D - band, 0));
+  return o[1] >= 2.19722457733621938f ? (int16_t)lo : (int16_t)-1;
+}
+
+// Per tile; an unconfident tile of the left border columns tx < t0 = ceil((D - 1) / 16), where the
+// full-range search has no valid pixel (and the network no label), takes the window of tile
+// (ty, t0).
+__global__ void k_band_tiles(const float* __restrict__ out, int th, int tw, int D, int band,
                              int16_t* __restrict__ tile_lo) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const float o0 = out[2 * i], z = out[2 * i + 1];
-  const float c = rintf(o0 * 16.0f) - (float)(band / 2);
-  const float hiv = (float)max(D - band, 0);
-  const float lo = fminf(fmaxf(c, 0.0f), hiv);
-  tile_lo[i] = z >= 2.19722457733621938f ? (int16_t)lo : (int16_t)-1;
+  if (i >= th * tw) return;
+  int16_t w = tile_window(out + 2 * i, D, band);
+  const int ty = i / tw, tx = i % tw, t0 = (D - 1 + 15) / 16;
+  if (w < 0 && tx < t0 && t0 < tw) w = tile_window(out + 2 * (ty * tw + t0), D, band);
+  tile_lo[i] = w;
 }
 
 }  // namespace
@@ -734,9 +742,9 @@ void launch_band_input(cudaStream_t s, const uint8_t* left, const uint8_t* right
                                                           reinterpret_cast<__nv_bfloat16*>(x));
 }
 
-void launch_band_tiles(cudaStream_t s, const float* cnn_out, int n, int D, int band_width,
+void launch_band_tiles(cudaStream_t s, const float* cnn_out, int th, int tw, int D, int band_width,
                        int16_t* tile_lo) {
-  k_band_tiles<<<(n + 255) / 256, 256, 0, s>>>(cnn_out, n, D, band_width, tile_lo);
+  k_band_tiles<<<(th * tw + 255) / 256, 256, 0, s>>>(cnn_out, th, tw, D, band_width, tile_lo);
 }
 
 }  // namespace pd
@@ -944,7 +952,7 @@ pd_status pd_band_tiles(pd_ctx* ctx, const float* cnn_out, int tiles_h, int tile
                 D, band_width);
   pd_status st = cuda_ok(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
   if (st != PD_OK) return st;
-  launch_band_tiles(ctx->stream, cnn_out, tiles_h * tiles_w, D, band_width, tile_lo);
+  launch_band_tiles(ctx->stream, cnn_out, tiles_h, tiles_w, D, band_width, tile_lo);
   return launched(ctx, "pd_band_tiles");
 }
 

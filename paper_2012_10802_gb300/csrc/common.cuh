@@ -143,7 +143,7 @@ bool cnn_fits(const pd_cnn* net, int B, int Hd, int Wd);
 const float* cnn_forward_enqueue(cudaStream_t s, pd_cnn* net, const void* x, int Hd, int Wd);
 void launch_band_input(cudaStream_t s, const uint8_t* left, const uint8_t* right, int W, int H,
                        size_t pitch, const int32_t* kappa, void* x);
-void launch_band_tiles(cudaStream_t s, const float* cnn_out, int n, int D, int band_width,
+void launch_band_tiles(cudaStream_t s, const float* cnn_out, int th, int tw, int D, int band_width,
                        int16_t* tile_lo);
 
 struct RoadCoefF {

@@ -188,6 +188,7 @@ def test_tiles_match_oracle(B, ctx):
     out[..., 1] = rng.normal(2.0, 1.5, size=(68, 120))
     out[0, :4, 1] = [np.float32(math.log(9.0)), np.nextafter(np.float32(math.log(9.0)), np.float32(0)), 5, 5]
     out[0, 2:4, 0] = [2.5 / 16 + 0.5, 0.15625]          # rint ties
+    out[5:9, :10, 1] = -3.0                             # unconfident tiles in the left border
     for D, band in [(128, 17), (32, 17), (64, 5), (16, 16)]:
         ref = bc.tile_windows(out, D, band)
         tl = B.pd_band_tiles(ctx, torch.from_numpy(out).cuda(), D, band)

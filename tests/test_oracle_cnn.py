@@ -163,3 +163,23 @@ def test_tile_windows_hand_cases():
     assert lo.tolist() == [[8, -1, 0, 0, 0, 111]]
     out[0, 3, 0] = 1.5625                              # 25 -> 17
     assert bc.tile_windows(out, 128)[0, 3] == 17
+
+
+def test_tile_windows_left_border_inherits():
+    """Unconfident tiles left of column D - 1 take the window of tile column ceil((D-1)/16)."""
+    ln9 = np.float32(math.log(9.0))
+    out = np.zeros((2, 12, 2), np.float32)
+    out[..., 0] = 1.25                                  # centre 20 -> window start 12
+    out[..., 1] = ln9
+    out[0, :3, 1] = 0.0                                 # unconfident, inside the border (t0 = 2 for D = 32)
+    out[1, 2, 1] = 0.0                                  # border tile column itself unconfident
+    out[1, 0, 1] = 0.0
+    out[0, 5, 1] = 0.0                                  # unconfident outside the border: full range
+    lo = bc.tile_windows(out, 32)                       # t0 = 2
+    assert lo[0, :3].tolist() == [-1, -1, -1]           # tile t0 unconfident: nothing to inherit
+    assert lo[1, :3].tolist() == [-1, 12, -1]
+    assert lo[0, 5] == -1                               # outside the border: full range
+    out[1, 2, 1] = ln9                                  # tile t0 of row 1 confident again
+    assert bc.tile_windows(out, 32)[1, :3].tolist() == [12, 12, 12]
+    lo = bc.tile_windows(out, 128)                      # t0 = 8: tiles 0..7 inherit from tile 8
+    assert lo[0, :8].tolist() == [12] * 8 and (lo[1] == 12).all()
