@@ -1,8 +1,10 @@
 // Band-restricted SGM: the matching cost, Eq. (8) aggregation, Eq. (9) winner and the left-right
 // check of Sec. II-B, each limited to a per-16x16-tile disparity window (an extension beyond the
 // paper: the windows come from the band network in cnn.cu, or from the caller).  Outside its
-// window a pixel's L is infinite; the volumes keep the full-range [H][W][D] interleaved layout, and
-// only the 16-disparity groups that meet a pixel's window are computed, read and written.
+// window a pixel's L is infinite.  The band's cost and L volumes are group-major,
+// [D/16][H][W][16 bytes] (interleaved byte order inside each group, as in the full-range path),
+// so that the groups of neighbouring pixels are neighbours in memory whatever their windows; only
+// the groups that meet a pixel's window are computed, read and written.
 #include "common.cuh"
 #include "sgm_body.cuh"
 
@@ -27,6 +29,7 @@ constexpr int kCostBandPix = 128;
 __global__ void __launch_bounds__(2 * kCostBandPix) k_cost_band(const uint32_t* __restrict__ cl,
                                                                 const uint32_t* __restrict__ cr,
                                                                 int W, int D, BandArgs band,
+                                                                size_t plane,
                                                                 uint8_t* __restrict__ cost) {
   __shared__ uint32_t sR[kCostBandPix + kMaxD];
   const int v = blockIdx.y;
@@ -59,7 +62,7 @@ __global__ void __launch_bounds__(2 * kCostBandPix) k_cost_band(const uint32_t* 
       }
       w[i] = packed;
     }
-    *reinterpret_cast<uint4*>(cost + ((size_t)v * W + u) * D + 16 * g) =
+    *reinterpret_cast<uint4*>(cost + plane * g + ((size_t)v * W + u) * 16) =
         make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
@@ -174,7 +177,8 @@ template <int GL, int NSM>
 __device__ __forceinline__ void agg_compact(const uint8_t* __restrict__ cost,
                                             uint8_t* __restrict__ dst, int W, int H, int D, int dx,
                                             int dy, uint32_t P1x2, uint32_t K21x2, int gw,
-                                            int warp, const BandArgs& band, uint4* s_ring) {
+                                            int warp, const BandArgs& band, uint4* s_ring,
+                                            size_t plane) {
   constexpr int LPW = 32 / GL;
   const int nlines = dy == 0 ? H : (dx == 0 ? W : W + H - 1);
   const int lane = threadIdx.x & 31;
@@ -184,7 +188,8 @@ __device__ __forceinline__ void agg_compact(const uint8_t* __restrict__ cost,
   if (first >= nlines) return;  // the whole warp leaves together
   const int line = first + stride * (lane / GL);
   const int last = min(first + stride * (LPW - 1), nlines - 1);
-  const LineWalk lw = line_walk(dx, dy, W, H, D, line, first, last, line < nlines);
+  // offsets of the line's pixels in 16-byte units of one group plane
+  const LineWalk lw = line_walk(dx, dy, W, H, 16, line, first, last, line < nlines);
 
   uint4* ring = s_ring + (size_t)warp * kCStages * NSM * 32 + lane;
   const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
@@ -193,8 +198,9 @@ __device__ __forceinline__ void agg_compact(const uint8_t* __restrict__ cost,
 
   // prefetch side: pointer to the prefetched pixel's group l, the window's group offset and the
   // number of slots to load, refreshed when the pixel enters a new tile
-  const uint8_t* pf_ptr = cost + lw.off0 + 16 * l;
-  int p_left = 0, p_off = 0, p_nl = 0;
+  const uint8_t* pf_ptr = cost + lw.off0 + plane * l;
+  int p_left = 0, p_nl = 0;
+  size_t p_off = 0;
   int pf_stage = 0;
   auto prefetch = [&](int sp) {
     if (sp >= lw.s_first && sp <= lw.s_last) {
@@ -202,7 +208,7 @@ __device__ __forceinline__ void agg_compact(const uint8_t* __restrict__ cost,
         int lo, hi;
         const int pu = lw.u0 + sp * dx, pv = lw.v0 + sp * dy;
         const Win w = window_of<GL>(band, pu, pv, D, lo, hi);
-        p_off = 16 * w.b;
+        p_off = plane * w.b;
         p_nl = w.ns - (GL * (w.ns - 1) + l >= w.ng ? 1 : 0);  // slots whose group is in the window
         p_left = steps_in_tile(pu, pv, dx, dy);
       }
@@ -210,7 +216,7 @@ __device__ __forceinline__ void agg_compact(const uint8_t* __restrict__ cost,
       const uint32_t dsts = ring_s + pf_stage * kStageBytes;
 #pragma unroll
       for (int i = 0; i < NSM; ++i)
-        if (i < p_nl) cp_async16(dsts + i * 32 * 16, pf_ptr + p_off + 16 * GL * i, 16u);
+        if (i < p_nl) cp_async16(dsts + i * 32 * 16, pf_ptr + p_off + plane * (GL * i), 16u);
     }
     cp_async_commit();
     pf_ptr += lw.delta;
@@ -228,8 +234,8 @@ __device__ __forceinline__ void agg_compact(const uint8_t* __restrict__ cost,
   // consumption side: window of the current pixel, refreshed per tile
   int c_left = 0;
   Win cw{0, NSM, NSM * GL};
-  uint8_t* st_ptr = dst + lw.off0 + 16 * l;
-  int st_off = 0;  // 16 * cw.b
+  uint8_t* st_ptr = dst + lw.off0 + plane * l;
+  size_t st_off = 0;  // plane * cw.b
   int stage = 0;
 
   int s = 0;
@@ -244,7 +250,7 @@ __device__ __forceinline__ void agg_compact(const uint8_t* __restrict__ cost,
         const int cu = lw.u0 + s * dx, cv = lw.v0 + s * dy;
         cw = window_of<GL>(band, cu, cv, D, lo, hi);
         c_left = steps_in_tile(cu, cv, dx, dy);
-        st_off = 16 * cw.b;
+        st_off = plane * cw.b;
       }
       --c_left;
     }
@@ -322,7 +328,7 @@ __device__ __forceinline__ void agg_compact(const uint8_t* __restrict__ cost,
           eq8_slot(N[i], prevHi, nextLo, ld ? rs[i * 32] : kOut4, K, P1x2, mp, Lw);
           if (i < ns_l) {
             m = __vminu2(m, min8(Lw));
-            if (ld) store8(st_ptr + st_off + 16 * GL * i, Lw);
+            if (ld) store8(st_ptr + st_off + plane * (GL * i), Lw);
 #pragma unroll
             for (int j = 0; j < 8; ++j) N[i][j] = Lw[j];
           }
@@ -391,7 +397,8 @@ __device__ __forceinline__ void agg_compact(const uint8_t* __restrict__ cost,
 template <int GL, int NSM>
 __global__ void __launch_bounds__(kCWarps * 32, NSM >= 4 ? 4 : 5) k_aggregate_band(
     const uint8_t* __restrict__ cost, uint8_t* __restrict__ out, int W, int H, int D, uint32_t dirs,
-    uint32_t P1x2, uint32_t K21x2, size_t vol_bytes, BandArgs band, int ntiles_smem) {
+    uint32_t P1x2, uint32_t K21x2, size_t vol_bytes, BandArgs band, int ntiles_smem,
+    size_t plane) {
   extern __shared__ uint4 s_dyn[];
   const int r = blockIdx.y;
   const uint32_t code = (dirs >> (4 * r)) & 0xfu;
@@ -405,7 +412,7 @@ __global__ void __launch_bounds__(kCWarps * 32, NSM >= 4 ? 4 : 5) k_aggregate_ba
     band.tile_lo = t;
   }
   agg_compact<GL, NSM>(cost, out + (size_t)r * vol_bytes, W, H, D, dx, dy, P1x2, K21x2,
-                       blockIdx.x * kCWarps + warp, warp, band, s_dyn);
+                       blockIdx.x * kCWarps + warp, warp, band, s_dyn, plane);
 }
 
 // 0xFFFF in every u16 half of word j whose disparity lies outside the window.
@@ -424,7 +431,7 @@ constexpr int kWtaBandPix = 64;
 
 __global__ void __launch_bounds__(2 * kWtaBandPix) k_wta_band(const uint8_t* __restrict__ vols,
                                                               int ndirs, size_t vol_bytes, int W,
-                                                              int D, BandArgs band,
+                                                              int D, BandArgs band, size_t plane,
                                                               int16_t* __restrict__ d_int,
                                                               float* __restrict__ dsub,
                                                               uint32_t* __restrict__ rkeys) {
@@ -444,11 +451,11 @@ __global__ void __launch_bounds__(2 * kWtaBandPix) k_wta_band(const uint8_t* __r
   if (pix < Peff) {
     band_window(band, u, v, D, lo, hi);
     const int b = lo >> 4, e = (hi - 1) >> 4;
-    const size_t off = ((size_t)v * W + u) * D;
+    const size_t off = ((size_t)v * W + u) * 16;
     for (int g = b + l; g <= e; g += 2) {
       const uint32_t in16 = group_in_mask(g, lo, hi);
       uint32_t sw[8], o[8];
-      load_S_il(vols, ndirs, vol_bytes, off + 16 * g, sw);
+      load_S_il(vols, ndirs, vol_bytes, off + plane * g, sw);
 #pragma unroll
       for (int j = 0; j < 8; ++j) sw[j] |= out_fill(in16, j);
       planar_to_natural(sw, o);
@@ -516,7 +523,7 @@ __global__ void k_lr_band(const int16_t* __restrict__ d_int, const float* __rest
 void launch_cost_band(cudaStream_t s, const uint32_t* cl, const uint32_t* cr, int W, int H, int D,
                       const BandArgs& band, uint8_t* cost) {
   k_cost_band<<<dim3((W + kCostBandPix - 1) / kCostBandPix, H), 2 * kCostBandPix, 0, s>>>(
-      cl, cr, W, D, band, cost);
+      cl, cr, W, D, band, (size_t)W * H * 16, cost);
 }
 
 constexpr int kMaxSmemTiles = 16384;  // 32 KB of window table in shared memory
@@ -536,7 +543,8 @@ void launch_compact(cudaStream_t s, dim3 grid, const uint8_t* cost_il, uint8_t* 
     attr_set = true;
   }
   k_aggregate_band<GL, NSM><<<grid, kCWarps * 32, smem, s>>>(cost_il, out, W, H, D, packed, P1x2,
-                                                             K21x2, vol_bytes, band, nsm);
+                                                             K21x2, vol_bytes, band, nsm,
+                                                             (size_t)W * H * 16);
 }
 
 void launch_aggregate_band(cudaStream_t s, const uint8_t* cost_il, int W, int H, int D,
@@ -578,7 +586,7 @@ void launch_wta_band(cudaStream_t s, const uint8_t* vols, int ndirs, size_t vol_
     attr_set = true;
   }
   k_wta_band<<<dim3((W + kWtaBandPix - 1) / kWtaBandPix, H), 2 * kWtaBandPix, smem, s>>>(
-      vols, ndirs, vol_bytes, W, D, band, d_int, dsub, rkeys);
+      vols, ndirs, vol_bytes, W, D, band, (size_t)W * H * 16, d_int, dsub, rkeys);
 }
 
 void launch_lr_band(cudaStream_t s, const int16_t* d_int, const float* dsub, const uint32_t* rkeys,
