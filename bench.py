@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-pair mixed batch")
     ap.add_argument("--no-band", action="store_true", help="skip the learned-band comparison")
+    ap.add_argument("--no-stream", action="store_true", help="skip the closed-loop drive")
     ap.add_argument("--band-size", default=None,
                     help="WxH: only time pd_sgm_band on a road of that size with every tile "
                          "banded around its full-range median (for profiling)")
@@ -236,6 +237,48 @@ def bench_batch(B, torch, synth, n_pairs=64, steps=5, seq_steps=2):
             "sequential_ms": ts, "sequential_frames_per_s": n_pairs / (ts * 1e-3),
             "sequential_Mdisp_s": disp / (ts * 1e-3) / 1e6, "speedup": ts / tb,
             "identical_to_sequential": bool(same)}
+
+
+def bench_stream(B, torch, synth, n=16):
+    """Closed-loop perspective transformation on a 1280x720 drive of n frames whose roll turns by
+    0.1 degree and whose road offset grows every frame: each frame's row shifts come from the
+    previous frame's device-resident fit (pd_run_pipeline_dev); the first frame uses the true
+    model.  Frames are rendered on the GPU beforehand; the whole sequence is timed with CUDA
+    events."""
+    W, H = 1280, 720
+    frames = synth.drive_sequence(W, H, n, 2)
+    pairs = [synth.render_torch(sc, "cuda") for sc in frames]
+    ctx = B.Context(torch.cuda.current_device())
+    p = B.default_params()
+    outs = B.make_outputs(ctx, W, H)
+    first = B.road_model_tensor(ctx, B.RoadModel.make(*synth.true_model(frames[0])))
+    model_dev = first.clone()
+    for _ in range(2):   # warm-up of the whole chain
+        model_dev.copy_(first)
+        for left, right in pairs[:3]:
+            B.pd_run_pipeline_dev(ctx, left, right, model_dev, p, outs)
+    torch.cuda.synchronize()
+    model_dev.copy_(first)
+    fits, ranges = [], []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    total = 0.0
+    for (left, right) in pairs:
+        e0.record()
+        B.pd_run_pipeline_dev(ctx, left, right, model_dev, p, outs)
+        model_dev.copy_(outs[1]["fitted"])
+        e1.record()
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+        fits.append(B.RoadModel.from_tensor(outs[1]["fitted"]))
+        d0 = outs[1]["d_int"][outs[1]["D1"] >= 0].float()
+        ranges.append(torch.quantile(d0, 0.99).item() - torch.quantile(d0, 0.01).item())
+    ctx.close()
+    import math
+    roll_err = [abs(math.degrees(f.roll - sc.roll)) for f, sc in zip(fits, frames)]
+    return {"workload": "closed-loop drive 1280x720 D=128 8 paths, %d frames, roll +0.1 deg and "
+                        "a0 +0.05 px per frame" % n,
+            "ms_per_frame": total / n, "max_roll_error_deg": max(roll_err),
+            "residual_range_px_p1_p99_max": max(ranges)}
 
 
 def band_only(B, torch, synth, size, steps, warmup):
@@ -474,12 +517,27 @@ def main():
                              "peak_source": "64 int instr/clk/SM (microbenchmark) x 2 u16 lanes "
                                             "x 152 SMs x %.0f MHz" % sm_max}}
 
+    # Sec. III accuracy of the benchmark frame against the generator's ground truth: disparity
+    # D1 against the true disparity, mask against the pixels deeper than delta_PD
+    acc = None
+    if rank == 0:
+        _, t = outs
+        D4 = torch.from_numpy(synth.gt_disparity(sc).astype(np.float32)).cuda()
+        gt = torch.from_numpy(synth.pothole_truth(sc, float(params.delta_pd)).astype(np.uint8)).cuda()
+        acc = B.pd_accuracy(ctx, t["D1"], D4, t["mask"], gt)
+        recs, ncomp = B.component_records(outs)
+        acc["components"] = ncomp
+        acc["kept_components"] = int(np.sum(recs["fake"] == 0)) if ncomp > 0 else 0
+
     batch = None
     if not args.no_batch and not args.size:
         batch = bench_batch(B, torch, synth)
     band_res = None
     if not args.no_band and not args.size:
         band_res = bench_band(B, torch, synth)
+    stream_res = None
+    if not args.no_stream and not args.size and rank == 0:
+        stream_res = bench_stream(B, torch, synth)
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -502,7 +560,8 @@ def main():
                    "stage_ms": {k: prof[k] / calls for k in ("prep_ms", "aggregate_ms",
                                                             "disparity_ms", "transform_ms",
                                                             "superpixel_ms", "mask_ms")},
-                   "wall_s": wall, "batch64": batch, "band1080": band_res},
+                   "wall_s": wall, "accuracy": acc, "batch64": batch, "band1080": band_res,
+                   "stream720": stream_res},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": prof["launches"], "clocks": clocks,
     }

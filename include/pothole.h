@@ -321,6 +321,18 @@ pd_status pd_components(pd_ctx* ctx, const uint8_t* mask, const int32_t* sp_labe
                         int connectivity, int32_t* labels, pd_component* comps, int max_comps,
                         int* n_comps);
 
+/* ------------------------------------------------ Sec. III: accuracy against a ground truth */
+
+/* Sec. III-A: over the q pixels with D1 >= 0 and a finite ground-truth disparity D4, the
+ * percentage of error pixels e_p = 100 #{|D1 - D4| > eps_k} / q for the three tolerances eps
+ * (host float [3]) and the RMSE e_r = sqrt(sum (D1 - D4)^2 / q); Sec. III-B: pixel precision,
+ * recall, accuracy and F-score of the pothole mask against a ground-truth mask (non-zero =
+ * pothole).  out (device, double [13]): q, e_p1, e_p2, e_p3, e_r, tp, fp, fn, tn, precision,
+ * recall, accuracy, F-score (NaN where a denominator is 0).  Counts are exact; the squared-error
+ * sum is accumulated in double precision in no fixed order. */
+pd_status pd_accuracy(pd_ctx* ctx, const float* D1, const float* D4, const uint8_t* mask,
+                      const uint8_t* gt_mask, int W, int H, const float* eps, double* out);
+
 /* -------------------------------------- learned disparity band (an extension of the paper) */
 
 /* Sec. II-A and II-B with the disparity search of each 16x16 tile restricted to a window:
@@ -414,6 +426,16 @@ pd_status pd_sgm_learned(pd_ctx* ctx, pd_cnn* net, const uint8_t* left, const ui
 pd_status pd_run_pipeline(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H,
                           size_t pitch, const pd_road_model* model, const pd_params* params,
                           const pd_outputs* out, pd_stage_times* times);
+
+/* Closed-loop form of pd_run_pipeline (Sec. II-A's perspective transformation driven by the road
+ * model fitted in Sec. II-C on the previous frame): the same steps, with the model for the row
+ * shifts read from device memory, so a stream of frames runs with no host round trip.  model_dev
+ * may be out->fitted itself (the fit of this frame then replaces it once the shifts are taken).
+ * A device model with an order other than 1 or 2 or a non-finite value gives zero shifts. */
+pd_status pd_run_pipeline_dev(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W,
+                              int H, size_t pitch, const pd_road_model* model_dev,
+                              const pd_params* params, const pd_outputs* out,
+                              pd_stage_times* times);
 
 #ifdef __cplusplus
 }

@@ -374,3 +374,37 @@ def components(labels, sp_labels, n):
     out = np.zeros((max(n, 1), 12), np.int64)
     lib().or_components(_ptr(lab), _ptr(_c(sp_labels, np.int32)), W, H, n, _ptr(out))
     return out[:n]
+
+
+# ----------------------------------------------------------------------------- Sec. III accuracy
+
+ACCURACY_FIELDS = ("q", "e_p1", "e_p2", "e_p3", "e_r", "tp", "fp", "fn", "tn", "precision",
+                   "recall", "accuracy", "fscore")
+
+
+def accuracy(D1, D4, mask, gt_mask, eps=(1.0, 2.0, 3.0)):
+    """Sec. III-A: the percentage of error pixels e_p = 100 / q * #{|D1 - D4| > eps} and the RMSE
+    e_r = sqrt(sum (D1 - D4)^2 / q) over the q pixels with a disparity (D1 >= 0) and a finite
+    ground truth D4; Sec. III-B: pixel precision, recall, accuracy and F-score of the pothole
+    mask against the ground-truth mask.  Returns a dict with ACCURACY_FIELDS (NaN where a
+    denominator is 0)."""
+    D1 = np.asarray(D1, np.float64)
+    D4 = np.asarray(D4, np.float64)
+    valid = (D1 >= 0) & np.isfinite(D4)
+    q = int(valid.sum())
+    diff = D1[valid] - D4[valid]
+    out = {"q": q}
+    for k, e in enumerate(eps, 1):
+        out["e_p%d" % k] = 100.0 * np.count_nonzero(np.abs(diff) > e) / q if q else float("nan")
+    out["e_r"] = float(np.sqrt(np.sum(diff * diff) / q)) if q else float("nan")
+    m = np.asarray(mask) != 0
+    g = np.asarray(gt_mask) != 0
+    tp, fp = int(np.sum(m & g)), int(np.sum(m & ~g))
+    fn, tn = int(np.sum(~m & g)), int(np.sum(~m & ~g))
+    out.update(tp=tp, fp=fp, fn=fn, tn=tn)
+    out["precision"] = tp / (tp + fp) if tp + fp else float("nan")
+    out["recall"] = tp / (tp + fn) if tp + fn else float("nan")
+    out["accuracy"] = (tp + tn) / (tp + fp + fn + tn)
+    p, r = out["precision"], out["recall"]
+    out["fscore"] = 2 * p * r / (p + r) if tp else float("nan")
+    return out

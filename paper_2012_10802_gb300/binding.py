@@ -108,6 +108,7 @@ SIGNATURES = {
     "pd_sgm_learned": [_P, _P, _P, _P, _i, _i, _z, C.POINTER(RoadModel), C.POINTER(Params), _i,
                        _P, _P, _P, _P],
     "pd_components": [_P, _P, _P, _i, _i, _i, _P, _P, _i, _P],
+    "pd_accuracy": [_P, _P, _P, _P, _P, _i, _i, _P, _P],
     "pd_moments": [_P, _P, _i, _i, _P],
     "pd_transform": [_P, _P, _i, _i, _i, _f, _P, _P],
     "pd_superpixels": [_P, _P, _i, _i, _i, _f, _i, _P, _P, _P, C.POINTER(_i)],
@@ -115,6 +116,8 @@ SIGNATURES = {
     "pd_run_pipeline": [_P, _P, _P, _i, _i, _z, C.POINTER(RoadModel), C.POINTER(Params),
                         C.POINTER(Outputs), C.POINTER(StageTimes)],
     "pd_transform_noalloc": [_P, _i, _i, _i, _f, _P, _P, _P],
+    "pd_run_pipeline_dev": [_P, _P, _P, _i, _i, _z, _P, C.POINTER(Params), C.POINTER(Outputs),
+                            C.POINTER(StageTimes)],
     "pd_batch_config": [_P, C.c_size_t, _i, _i],
     "pd_sgm_batch": [_P, C.POINTER(Pair), _i, C.POINTER(Params)],
     "pd_profile_enable": [_P, _i],
@@ -312,6 +315,23 @@ def pd_components(ctx, mask, sp_labels, connectivity=8, max_comps=4096, labels=N
     count = int(n.item())
     recs = comps.cpu().numpy().view(COMPONENT_DTYPE)[:max(0, min(count, max_comps))]
     return labels, recs, count
+
+
+ACCURACY_FIELDS = ("q", "e_p1", "e_p2", "e_p3", "e_r", "tp", "fp", "fn", "tn", "precision",
+                   "recall", "accuracy", "fscore")
+
+
+def pd_accuracy(ctx, D1, D4, mask, gt_mask, eps=(1.0, 2.0, 3.0)):
+    """Sec. III accuracy of D1 against D4 and of the mask against gt_mask: a dict of
+    ACCURACY_FIELDS (synchronises the stream)."""
+    H, W = D1.shape
+    e = (C.c_float * 3)(*[float(x) for x in eps])
+    out = ctx.empty((13,), torch.float64)
+    ctx.check(lib().pd_accuracy(ctx.h, _ptr(D1), _ptr(D4), _ptr(mask), _ptr(gt_mask), W, H,
+                                C.cast(e, C.c_void_p), _ptr(out)))
+    vals = out.cpu().numpy()
+    return {k: (int(v) if k in ("q", "tp", "fp", "fn", "tn") else float(v))
+            for k, v in zip(ACCURACY_FIELDS, vals)}
 
 
 class Cnn:
@@ -515,6 +535,25 @@ def pd_run_pipeline(ctx, left, right, model, params, outputs, times=False):
                                     C.byref(params), C.byref(o),
                                     C.byref(st) if times else None))
     return st
+
+
+def pd_run_pipeline_dev(ctx, left, right, model_dev, params, outputs, times=False):
+    """pd_run_pipeline with the road model in device memory (model_dev: a uint8 tensor holding one
+    pd_road_model, e.g. outputs[1]["fitted"] of the previous frame, which may be updated in
+    place)."""
+    H, W = left.shape
+    o, _ = outputs
+    st = StageTimes() if times else None
+    ctx.check(lib().pd_run_pipeline_dev(ctx.h, _ptr(left), _ptr(right), W, H, W, _ptr(model_dev),
+                                        C.byref(params), C.byref(o),
+                                        C.byref(st) if times else None))
+    return st
+
+
+def road_model_tensor(ctx, model):
+    """One pd_road_model in device memory (uint8 tensor) from a host RoadModel."""
+    raw = np.frombuffer(bytes(model), np.uint8).copy()
+    return torch.from_numpy(raw).to(ctx.device)
 
 
 def pd_profile_enable(ctx, on=True):

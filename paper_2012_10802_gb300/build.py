@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpothole.so")
-SOURCES = ["api.cu", "sgm.cu", "dt.cu", "detect.cu", "batch.cu", "band.cu", "cnn.cu", "ccl.cu"]
+SOURCES = ["api.cu", "sgm.cu", "dt.cu", "detect.cu", "batch.cu", "band.cu", "cnn.cu", "ccl.cu", "report.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC,-O2",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

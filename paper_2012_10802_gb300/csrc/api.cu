@@ -176,17 +176,22 @@ pd_status check_sgm_params(pd_ctx* ctx, const pd_params* p) {
 }
 
 // Enqueues the fused SGM (no validation; scratch already sized).
+// The model is a host struct, or (model_dev != nullptr) one in device memory.
 pd_status sgm_enqueue(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H,
                       size_t pitch, const pd_road_model* model, const pd_params* p,
-                      int32_t* kappa, int16_t* d_int, float* D1, pd_prof_rec* rec) {
+                      int32_t* kappa, int16_t* d_int, float* D1, pd_prof_rec* rec,
+                      const pd_road_model* model_dev = nullptr) {
   cudaStream_t s = ctx->stream;
   SgmScratch sc = sgm_carve(ctx->ws, W, H, p->D, p->paths);
   int32_t* kap = kappa ? kappa : sc.kappa;
   size_t N = (size_t)W * H;
   size_t vol = N * p->D;
   mark(ctx, rec, 0);
-  launch_kappa(s, W, H, model->order, model->a, cos(model->roll), sin(model->roll),
-               (double)p->delta_pt, kap);
+  if (model_dev)
+    launch_kappa_dev(s, W, H, model_dev, (double)p->delta_pt, kap);
+  else
+    launch_kappa(s, W, H, model->order, model->a, cos(model->roll), sin(model->roll),
+                 (double)p->delta_pt, kap);
   launch_census(s, left, W, H, pitch, nullptr, sc.cl);
   launch_census(s, right, W, H, pitch, kap, sc.cr);
   launch_cost(s, sc.cl, sc.cr, W, H, p->D, 1, sc.cost);
@@ -838,12 +843,48 @@ pd_status pd_components(pd_ctx* ctx, const uint8_t* mask, const int32_t* sp_labe
   return launched(ctx, "pd_components");
 }
 
+pd_status pd_accuracy(pd_ctx* ctx, const float* D1, const float* D4, const uint8_t* mask,
+                      const uint8_t* gt_mask, int W, int H, const float* eps, double* out) {
+  PD_TRY(begin(ctx));
+  PD_TRY(check_image(ctx, W, H, (size_t)W));
+  PD_REQUIRE(D1 && D4 && mask && gt_mask && eps && out, "NULL input or output");
+  PD_REQUIRE(isfinite(eps[0]) && isfinite(eps[1]) && isfinite(eps[2]), "non-finite tolerance");
+  PD_TRY(ensure_ws(ctx, accuracy_scratch_bytes()));
+  count_launches(ctx, launch_accuracy(ctx->stream, D1, D4, mask, gt_mask, W, H, eps, out,
+                                      ctx->ws));
+  return launched(ctx, "pd_accuracy");
+}
+
+namespace {
+
+pd_status pipeline_impl(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H,
+                        size_t pitch, const pd_road_model* model, const pd_road_model* model_dev,
+                        const pd_params* p, const pd_outputs* out, pd_stage_times* times);
+
+}  // namespace
+
 pd_status pd_run_pipeline(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H,
                           size_t pitch, const pd_road_model* model, const pd_params* p,
                           const pd_outputs* out, pd_stage_times* times) {
   PD_TRY(begin(ctx));
-  PD_TRY(check_image(ctx, W, H, pitch));
   PD_TRY(check_model(ctx, model));
+  return pipeline_impl(ctx, left, right, W, H, pitch, model, nullptr, p, out, times);
+}
+
+pd_status pd_run_pipeline_dev(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W,
+                              int H, size_t pitch, const pd_road_model* model_dev,
+                              const pd_params* p, const pd_outputs* out, pd_stage_times* times) {
+  PD_TRY(begin(ctx));
+  PD_REQUIRE(model_dev != nullptr, "model is NULL");
+  return pipeline_impl(ctx, left, right, W, H, pitch, nullptr, model_dev, p, out, times);
+}
+
+namespace {
+
+pd_status pipeline_impl(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H,
+                        size_t pitch, const pd_road_model* model, const pd_road_model* model_dev,
+                        const pd_params* p, const pd_outputs* out, pd_stage_times* times) {
+  PD_TRY(check_image(ctx, W, H, pitch));
   PD_TRY(check_sgm_params(ctx, p));
   PD_REQUIRE(W <= kMaxImage && H <= kMaxImage, "the pipeline needs W, H <= %d", kMaxImage);
   PD_REQUIRE(left && right && out, "NULL input or outputs");
@@ -879,7 +920,7 @@ pd_status pd_run_pipeline(pd_ctx* ctx, const uint8_t* left, const uint8_t* right
   pd_prof_rec* rec = prof_begin(ctx);
   if (times) cudaEventRecord(ctx->ev[0], s);
   PD_TRY(sgm_enqueue(ctx, left, right, W, H, pitch, model, p, out->kappa, out->d_int, out->D1,
-                     rec));
+                     rec, model_dev));
   if (times) cudaEventRecord(ctx->ev[1], s);
   PD_TRY(transform_enqueue(ctx, out->D1, W, H, p->model_order, p->delta_dt, out->fitted,
                            out->D2, ctx->ws));
@@ -909,6 +950,8 @@ pd_status pd_run_pipeline(pd_ctx* ctx, const uint8_t* left, const uint8_t* right
   }
   return PD_OK;
 }
+
+}  // namespace
 
 pd_status pd_profile_enable(pd_ctx* ctx, int on) {
   if (!ctx) return PD_ERR_INVALID_ARG;

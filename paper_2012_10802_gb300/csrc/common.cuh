@@ -83,6 +83,8 @@ DirSet one_dir(int dx, int dy);
 // ------------------------------------------------------------------ SGM launchers (sgm.cu)
 void launch_kappa(cudaStream_t s, int W, int H, int order, const double a[3], double cs,
                   double sn, double delta_pt, int32_t* kappa);
+void launch_kappa_dev(cudaStream_t s, int W, int H, const pd_road_model* model, double delta_pt,
+                      int32_t* kappa);
 void launch_warp(cudaStream_t s, const uint8_t* right, int W, int H, size_t pitch,
                  const int32_t* kappa, uint8_t* out);
 // Census of img, or of the row-shifted image when kappa != nullptr.
@@ -137,6 +139,12 @@ void launch_lr_band(cudaStream_t s, const int16_t* d_int, const float* dsub, con
 size_t ccl_scratch_bytes(int W, int H, int max_comps);
 int launch_ccl(cudaStream_t s, const uint8_t* mask, const int32_t* sp, int W, int H, int conn,
                int32_t* labels, pd_component* comps, int max_comps, int* n_comps, void* scratch);
+
+// Accuracy report against a ground truth (report.cu).
+size_t accuracy_scratch_bytes();
+int launch_accuracy(cudaStream_t s, const float* D1, const float* D4, const uint8_t* mask,
+                    const uint8_t* gt, int W, int H, const float eps[3], double* out,
+                    void* scratch);
 
 // The band network (cnn.cu).
 bool cnn_fits(const pd_cnn* net, int B, int Hd, int Wd);

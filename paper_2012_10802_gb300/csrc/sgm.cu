@@ -28,6 +28,26 @@ __global__ void k_kappa(int W, int H, int order, double a0, double a1, double a2
   kappa_row(W, H, order, a0, a1, a2, cs, sn, delta_pt, kappa, v, threadIdx.x & 31);
 }
 
+// Eq. (6) with the road model read from device memory (for instance the previous frame's fit):
+// cos and sin of the roll are evaluated on the device.  A model with an order other than 1 or 2
+// or a non-finite coefficient gives kappa = 0 (no shift).
+__global__ void k_kappa_dev(int W, int H, const pd_road_model* __restrict__ m, double delta_pt,
+                            int32_t* __restrict__ kappa) {
+  const int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (v >= H) return;
+  const pd_road_model mm = *m;
+  const bool ok = (mm.order == 1 || mm.order == 2) && isfinite(mm.a[0]) && isfinite(mm.a[1]) &&
+                  isfinite(mm.a[2]) && isfinite(mm.roll);
+  if (!ok) {
+    if ((threadIdx.x & 31) == 0) kappa[v] = 0;
+    return;
+  }
+  double sn, cs;
+  sincos(mm.roll, &sn, &cs);
+  kappa_row(W, H, mm.order, mm.a[0], mm.a[1], mm.order == 2 ? mm.a[2] : 0.0, cs, sn, delta_pt,
+            kappa, v, threadIdx.x & 31);
+}
+
 __global__ void k_census(const uint8_t* __restrict__ img, int W, int H, size_t pitch,
                          const int32_t* __restrict__ kappa, uint32_t* __restrict__ codes) {
   census_tile(img, W, H, pitch, kappa, codes, blockIdx.x, blockIdx.y);
@@ -177,6 +197,11 @@ DirSet one_dir(int dx, int dy) {
 void launch_kappa(cudaStream_t s, int W, int H, int order, const double a[3], double cs,
                   double sn, double delta_pt, int32_t* kappa) {
   k_kappa<<<(H + 3) / 4, 128, 0, s>>>(W, H, order, a[0], a[1], a[2], cs, sn, delta_pt, kappa);
+}
+
+void launch_kappa_dev(cudaStream_t s, int W, int H, const pd_road_model* model, double delta_pt,
+                      int32_t* kappa) {
+  k_kappa_dev<<<(H + 3) / 4, 128, 0, s>>>(W, H, model, delta_pt, kappa);
 }
 
 void launch_warp(cudaStream_t s, const uint8_t* right, int W, int H, size_t pitch,

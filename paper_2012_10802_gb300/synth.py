@@ -217,3 +217,18 @@ def render_torch(scene: Scene, device="cuda"):
     val = val + torch.randn((H, W), generator=g, device=device, dtype=torch.float64) * scene.noise_sigma
     right = torch.clamp(torch.round(val), 0, 255).to(torch.uint8)
     return left.contiguous(), right.contiguous()
+
+
+def drive_sequence(W, H, n, seed, roll_step_deg=0.1, a0_step=0.05, hole_step=2.0):
+    """n consecutive frames of a drive: the 720p-style road scaled to W x H whose roll turns by
+    roll_step_deg and whose a0 grows by a0_step per frame, with the potholes moving down the image
+    by hole_step rows per frame (each frame's noise drawn from its own seed)."""
+    base = road_scaled(W, H, seed)
+    frames = []
+    for t in range(n):
+        a = (base.a[0] + a0_step * t, base.a[1], base.a[2])
+        holes = [Pothole(p.cu, p.cv + hole_step * t, p.ax, p.ay, p.depth) for p in base.potholes
+                 if p.cv + hole_step * t + p.ay < H]
+        frames.append(Scene(W, H, a, base.roll + np.deg2rad(roll_step_deg) * t, holes,
+                            base.noise_sigma, seed * 1000 + t))
+    return frames
