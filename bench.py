@@ -110,6 +110,32 @@ class Clocks:
                 "samples": len(sm)}
 
 
+# ---------------------------------------------------------------- several ranks (replicas only)
+# Frames are independent: each rank processes its own frame with no data-path collective, and
+# only the timing is combined.  These helpers are the host logic of that path (tested with gloo
+# ranks on the CPU).
+
+def rank_seed(rank):
+    """Seed of the synthetic pair of a rank (rank 0 runs the 720p benchmark road, seed 2)."""
+    return 2 + rank
+
+
+def max_over_ranks(value, dist, device):
+    """The largest of the ranks' values (the slowest rank bounds the job); value itself without a
+    process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mdisp(steps, world, W, H, D, t_ms):
+    """Whole-job throughput: the disparities of every rank's frames over the slowest rank's time."""
+    return steps * world * W * H * D / (t_ms * 1e-3) / 1e6
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -415,8 +441,8 @@ def main():
         torch.cuda.synchronize()
 
     # inputs: one synthetic pair per rank (independent frames: weak scaling, no collective)
-    sc = synth.road_1280x720(seed=2 + rank) if (W_, H_) == (1280, 720) else \
-        synth.road_scaled(W_, H_, seed=2 + rank)
+    sc = synth.road_1280x720(seed=rank_seed(rank)) if (W_, H_) == (1280, 720) else \
+        synth.road_scaled(W_, H_, seed=rank_seed(rank))
     left_np, right_np = synth.render(sc)
     model = B.RoadModel.make(*synth.true_model(sc))
     params = B.default_params()
@@ -447,12 +473,8 @@ def main():
     prof = B.pd_profile_read(ctx)
     B.pd_profile_enable(ctx, False)
     dev_ms = sum(a.elapsed_time(b) for a, b in ev)
-    t_max = dev_ms
-    if dist:
-        t = torch.tensor([dev_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = args.steps * world * W_ * H_ * D_ / (t_max * 1e-3) / 1e6
+    t_max = max_over_ranks(dev_ms, dist, "cuda")
+    value = whole_job_mdisp(args.steps, world, W_, H_, D_, t_max)
 
     # ---- end to end through the public API: pinned host inputs in, the mask back out
     e2e = None
@@ -476,12 +498,8 @@ def main():
             mh.copy_(outs[1]["mask"], non_blocking=True)
         e1.record()
         barrier()
-        e2e_ms = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([e2e_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e = {"value": args.steps * world * W_ * H_ * D_ / (e2e_ms * 1e-3) / 1e6,
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+        e2e = {"value": whole_job_mdisp(args.steps, world, W_, H_, D_, e2e_ms),
                "unit": "Mdisp/s", "h2d_bytes_per_step": 2 * W_ * H_,
                "d2h_bytes_per_step": W_ * H_, "ms_per_step": e2e_ms / args.steps}
 

@@ -68,6 +68,8 @@ typedef struct {
   int slic_iters;     /* SLIC iterations [10] */
   int model_order;    /* road model fitted by the transform, 1 or 2 [2] */
   int threshold_mode; /* 0: t_s = road mean - delta_pd [0]; 1: t_s = t_r - delta_pd */
+  int fit_iters;      /* robust refits of the road model on the inliers of the previous fit [0] */
+  float fit_tau;      /* inlier band |D1 - f| <= fit_tau of those refits, pixels [1] */
 } pd_params;
 
 /* One connected component of the pothole mask (56 bytes). */
@@ -202,6 +204,13 @@ pd_status pd_sgm(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, 
 
 /* ----------------------------------------------------- Sec. II-C: disparity transformation */
 
+/* pd_transform with `iters` refits of the road model, each on the pixels within tau of the
+ * previous fit (|D1 - f| <= tau, f in single precision as in Eq. (13)): potholes deeper than tau
+ * stop pulling the fitted road towards them.  iters = 0 is pd_transform.  iters in 0..16. */
+pd_status pd_transform_robust(pd_ctx* ctx, const float* D1, int W, int H, int order,
+                              float delta_dt, int iters, float tau, pd_road_model* fitted,
+                              float* D2);
+
 /* Exact sums the road fit needs over the pixels with D1 >= 0, with q = rint(1024 D1) and doubled
  * centred coordinates u~ = 2u - (W-1), v~ = 2v - (H-1): count, sum u~^i v~^j (i + j <= 4),
  * sum q u~^i v~^j (i + j <= 2) and sum q^2, in that order (i outer, j inner), each a signed
@@ -213,7 +222,8 @@ pd_status pd_moments(pd_ctx* ctx, const float* D1, int W, int H, int64_t* sums);
  * for order 1, 0.01-degree grid over +-15 degrees refined by golden-section search for order 2;
  * coefficients by Eq. (11)), then D2 = max(0, D1 - f + delta_dt) in single precision, with
  * delta_dt at invalid pixels.  The fit stays on the device (no host round trip).
- * fitted: one pd_road_model (device, may be NULL); D2: float [H][W].  W, H <= 4096. */
+ * fitted: one pd_road_model (device, 8-byte aligned, may be NULL; written whole, padding zero);
+ * D2: float [H][W].  W, H <= 4096. */
 pd_status pd_transform(pd_ctx* ctx, const float* D1, int W, int H, int order, float delta_dt,
                        pd_road_model* fitted, float* D2);
 

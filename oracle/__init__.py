@@ -66,6 +66,7 @@ def _declare(L):
         "or_superpixel_mean": (None, [_P, _P, _i, _i, _i, _P]),
         "or_threshold": (_i, [_P, _P, _i, _i, _f, _i, C.POINTER(_d), C.POINTER(_d), _P]),
         "or_mask": (None, [_P, _i, _i, _d, _P]),
+        "or_fit_road_robust": (None, [_P, _i, _i, _i, _i, _f, C.POINTER(RoadModel)]),
         "or_ccl": (_i, [_P, _i, _i, _i, _P]),
         "or_components": (None, [_P, _P, _i, _i, _i, _P]),
         "or_band_windows": (None, [_P, _i, _i, _i, _i, _P, _P]),
@@ -408,3 +409,12 @@ def accuracy(D1, D4, mask, gt_mask, eps=(1.0, 2.0, 3.0)):
     p, r = out["precision"], out["recall"]
     out["fscore"] = 2 * p * r / (p + r) if tp else float("nan")
     return out
+
+
+def fit_robust(D1, order, iters, tau):
+    """Sec. II-C's fit followed by `iters` refits on the inliers within tau (reading R17)."""
+    D1 = _c(D1, np.float32)
+    H, W = D1.shape
+    m = RoadModel()
+    lib().or_fit_road_robust(_ptr(D1), W, H, order, iters, float(tau), C.byref(m))
+    return m

@@ -22,6 +22,7 @@
  *   R14 connected components of the mask: 8- or 4-connectivity, labelled by their smallest
  *       raster index (Sec. II-E names CCL only);
  *   R15 fake potholes (Sec. III-B): centroid in a corner cell of an 8 x 8 split, or one superpixel;
+ *   R17 robust road fit (beyond Sec. II-C): refits on the inliers |D1 - f| <= tau of the previous fit;
  *   R10 (band SGM, beyond the paper) per-16x16-tile windows [lo, lo + band) clipped to [0, D),
  *       L = +infinity outside the window, minima of Eq. (8) over the previous pixel's window,
  *       winners and right views over in-window candidates, valid pixels need u >= hi - 1.
@@ -922,5 +923,47 @@ void or_components(const int32_t* labels, const int32_t* sp, int W, int H, int n
     o[10] = !multi;
     o[11] = corner || !multi;
     ++k;
+  }
+}
+
+/* ------------------------------------------------------- robust road fit (beyond Sec. II-C) */
+
+/* Reading R17: the moments of Sec. II-C over the inliers of a previous fit only: pixels with
+ * D1 >= 0 and |D1 - f(p)| <= tau, f evaluated in single precision exactly as in the transform. */
+void or_moments_inliers(const float* D1, int W, int H, const or_road_model* fit, float tau,
+                        or_moment_sums* out) {
+  float c = (float)cos(fit->roll), s = (float)sin(fit->roll);
+  float a0 = (float)fit->a[0], a1 = (float)fit->a[1];
+  float a2 = fit->order == 2 ? (float)fit->a[2] : 0.0f;
+  float uc = (float)((double)(W - 1) * 0.5), vc = (float)((double)(H - 1) * 0.5);
+  size_t n = (size_t)W * H;
+  float* masked = (float*)malloc(sizeof(float) * n);
+  for (int v = 0; v < H; ++v)
+    for (int u = 0; u < W; ++u) {
+      size_t p = (size_t)v * W + u;
+      float d1 = D1[p];
+      masked[p] = -1.0f;
+      if (!(d1 >= 0.0f)) continue;
+      float t1 = ((float)v - vc) * c;
+      float t2 = ((float)u - uc) * s;
+      float vp = (t1 - t2) + vc;
+      float f = (a0 + a1 * vp) + a2 * (vp * vp);
+      if (fabsf(d1 - f) <= tau) masked[p] = d1;
+    }
+  or_moments(masked, W, H, out);
+  free(masked);
+}
+
+/* The fit of Sec. II-C followed by `iters` refits on the inliers (within tau) of the previous
+ * fit. */
+void or_fit_road_robust(const float* D1, int W, int H, int order, int iters, float tau,
+                        or_road_model* fitted) {
+  or_moment_sums m;
+  or_moments(D1, W, H, &m);
+  or_fit_road(&m, order, W, H, fitted);
+  for (int k = 0; k < iters; ++k) {
+    or_road_model prev = *fitted;
+    or_moments_inliers(D1, W, H, &prev, tau, &m);
+    or_fit_road(&m, order, W, H, fitted);
   }
 }

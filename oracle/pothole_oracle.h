@@ -112,6 +112,13 @@ int or_ccl(const uint8_t* mask, int W, int H, int conn, int32_t* labels);
 void or_components(const int32_t* labels, const int32_t* sp, int W, int H, int ncomp,
                    int64_t* out);
 
+/* Robust road fit (reading R17): moments over the inliers of a previous fit, and the fit
+ * iterated on them. */
+void or_moments_inliers(const float* D1, int W, int H, const or_road_model* fit, float tau,
+                        or_moment_sums* out);
+void or_fit_road_robust(const float* D1, int W, int H, int order, int iters, float tau,
+                        or_road_model* fitted);
+
 /* Test-harness helpers: the size of or_moment_sums, and its 23 sums as (low, high) 64-bit pairs. */
 size_t or_moment_sums_size(void);
 void or_moments_export(const or_moment_sums* mom, int64_t* out);

@@ -48,7 +48,8 @@ class Params(C.Structure):
     _fields_ = [("D", C.c_int), ("paths", C.c_int), ("P1", C.c_int), ("P2", C.c_int),
                 ("lr_tol", C.c_int), ("delta_pt", C.c_float), ("delta_dt", C.c_float),
                 ("delta_pd", C.c_float), ("slic_K", C.c_int), ("slic_m", C.c_float),
-                ("slic_iters", C.c_int), ("model_order", C.c_int), ("threshold_mode", C.c_int)]
+                ("slic_iters", C.c_int), ("model_order", C.c_int), ("threshold_mode", C.c_int),
+                ("fit_iters", C.c_int), ("fit_tau", C.c_float)]
 
 
 class Outputs(C.Structure):
@@ -109,6 +110,7 @@ SIGNATURES = {
                        _P, _P, _P, _P],
     "pd_components": [_P, _P, _P, _i, _i, _i, _P, _P, _i, _P],
     "pd_accuracy": [_P, _P, _P, _P, _P, _i, _i, _P, _P],
+    "pd_transform_robust": [_P, _P, _i, _i, _i, _f, _i, _f, _P, _P],
     "pd_moments": [_P, _P, _i, _i, _P],
     "pd_transform": [_P, _P, _i, _i, _i, _f, _P, _P],
     "pd_superpixels": [_P, _P, _i, _i, _i, _f, _i, _P, _P, _P, C.POINTER(_i)],
@@ -469,6 +471,17 @@ def pd_transform(ctx, D1, order, delta_dt, fitted=None, D2=None):
         D2 = ctx.empty((H, W), torch.float32)
     ctx.check(lib().pd_transform(ctx.h, _ptr(D1), W, H, order, float(delta_dt), _ptr(fitted),
                                  _ptr(D2)))
+    return fitted, D2
+
+
+def pd_transform_robust(ctx, D1, order, delta_dt, iters, tau, fitted=None, D2=None):
+    H, W = D1.shape
+    if fitted is None:
+        fitted = ctx.empty((C.sizeof(RoadModel),), torch.uint8)
+    if D2 is None:
+        D2 = ctx.empty((H, W), torch.float32)
+    ctx.check(lib().pd_transform_robust(ctx.h, _ptr(D1), W, H, order, float(delta_dt), int(iters),
+                                        float(tau), _ptr(fitted), _ptr(D2)))
     return fitted, D2
 
 

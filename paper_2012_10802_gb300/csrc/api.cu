@@ -240,21 +240,31 @@ size_t transform_scratch_bytes(int W, int H) {
   carve_size<int64_t>(acc, 46);
   carve_size<pd_road_model>(acc, 1);
   carve_size<RoadCoefF>(acc, 1);
+  carve_size<RoadCoefF>(acc, 1);
   carve_size<uint8_t>(acc, roll_scratch_bytes());
   return acc;
 }
 
+// Sec. II-C: the fit, then `iters` refits on the inliers (|D1 - f| <= tau) of the previous fit
+// (reading R17; 0 iterations is the paper's fit), then Eq. (13).
 pd_status transform_enqueue(pd_ctx* ctx, const float* D1, int W, int H, int order,
-                            float delta_dt, pd_road_model* fitted, float* D2, void* base) {
+                            float delta_dt, pd_road_model* fitted, float* D2, void* base,
+                            int iters = 0, float tau = 0.0f) {
   Carve c(base);
   void* part = c.take<uint8_t>(moments_scratch_bytes(W, H));
   int64_t* sums = c.take<int64_t>(46);
   pd_road_model* fit = c.take<pd_road_model>(1);
   RoadCoefF* coef = c.take<RoadCoefF>(1);
+  RoadCoefF* prev = c.take<RoadCoefF>(1);
   double* grid = reinterpret_cast<double*>(c.take<uint8_t>(roll_scratch_bytes()));
   cudaStream_t s = ctx->stream;
   launch_moments(s, D1, W, H, part, sums);
   int n = launch_roll_solve(s, sums, order, W, H, fitted ? fitted : fit, coef, grid);
+  for (int k = 0; k < iters; ++k) {
+    cudaMemcpyAsync(prev, coef, sizeof(RoadCoefF), cudaMemcpyDeviceToDevice, s);
+    launch_moments(s, D1, W, H, part, sums, prev, tau);
+    n += 2 + launch_roll_solve(s, sums, order, W, H, fitted ? fitted : fit, coef, grid);
+  }
   launch_d2(s, D1, W, H, coef, delta_dt, D2);
   count_launches(ctx, 3 + n);
   return launched(ctx, "pd_transform");
@@ -597,6 +607,8 @@ pd_status pd_default_params(pd_params* p) {
   p->slic_iters = 10;
   p->model_order = 2;
   p->threshold_mode = 0;
+  p->fit_iters = 0;
+  p->fit_tau = 1.0f;
   return PD_OK;
 }
 
@@ -775,6 +787,22 @@ pd_status pd_sgm_learned(pd_ctx* ctx, pd_cnn* net, const uint8_t* left, const ui
                           prof_begin(ctx));
 }
 
+pd_status pd_transform_robust(pd_ctx* ctx, const float* D1, int W, int H, int order,
+                              float delta_dt, int iters, float tau, pd_road_model* fitted,
+                              float* D2) {
+  PD_TRY(begin(ctx));
+  PD_TRY(check_image(ctx, W, H, (size_t)W));
+  PD_REQUIRE(W <= kMaxImage && H <= kMaxImage, "transform needs W, H <= %d", kMaxImage);
+  PD_REQUIRE(D1 && D2, "NULL input or output");
+  PD_REQUIRE(order == 1 || order == 2, "order %d must be 1 or 2", order);
+  PD_REQUIRE(isfinite(delta_dt), "delta_dt must be finite");
+  PD_REQUIRE(iters >= 0 && iters <= 16, "iters = %d must be in 0..16", iters);
+  PD_REQUIRE(isfinite(tau) && tau > 0.0f, "tau must be positive");
+  PD_REQUIRE((reinterpret_cast<uintptr_t>(fitted) & 7u) == 0, "fitted must be 8-byte aligned");
+  PD_TRY(ensure_ws(ctx, transform_scratch_bytes(W, H)));
+  return transform_enqueue(ctx, D1, W, H, order, delta_dt, fitted, D2, ctx->ws, iters, tau);
+}
+
 pd_status pd_moments(pd_ctx* ctx, const float* D1, int W, int H, int64_t* sums) {
   PD_TRY(begin(ctx));
   PD_TRY(check_image(ctx, W, H, (size_t)W));
@@ -793,6 +821,7 @@ pd_status pd_transform(pd_ctx* ctx, const float* D1, int W, int H, int order, fl
   PD_REQUIRE(D1 && D2, "NULL input or output");
   PD_REQUIRE(order == 1 || order == 2, "order %d must be 1 or 2", order);
   PD_REQUIRE(isfinite(delta_dt), "delta_dt must be finite");
+  PD_REQUIRE((reinterpret_cast<uintptr_t>(fitted) & 7u) == 0, "fitted must be 8-byte aligned");
   PD_TRY(ensure_ws(ctx, transform_scratch_bytes(W, H)));
   return transform_enqueue(ctx, D1, W, H, order, delta_dt, fitted, D2, ctx->ws);
 }
@@ -890,6 +919,9 @@ pd_status pipeline_impl(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, 
   PD_REQUIRE(left && right && out, "NULL input or outputs");
   PD_REQUIRE(out->d_int && out->D1 && out->D2 && out->labels && out->D3 && out->mask,
              "pd_outputs is missing a required buffer");
+  PD_REQUIRE((reinterpret_cast<uintptr_t>(out->fitted) & 7u) == 0 &&
+                 (reinterpret_cast<uintptr_t>(model_dev) & 7u) == 0,
+             "road models in device memory must be 8-byte aligned");
   PD_REQUIRE(p->model_order == 1 || p->model_order == 2, "model_order must be 1 or 2");
   PD_REQUIRE(p->slic_K >= 1 && (size_t)p->slic_K <= (size_t)W * H, "slic_K out of range");
   PD_REQUIRE(isfinite(p->slic_m) && p->slic_m > 0.0f, "slic_m must be positive");
@@ -922,8 +954,10 @@ pd_status pipeline_impl(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, 
   PD_TRY(sgm_enqueue(ctx, left, right, W, H, pitch, model, p, out->kappa, out->d_int, out->D1,
                      rec, model_dev));
   if (times) cudaEventRecord(ctx->ev[1], s);
+  PD_REQUIRE(p->fit_iters >= 0 && p->fit_iters <= 16 && isfinite(p->fit_tau) && p->fit_tau > 0.0f,
+             "fit_iters must be in 0..16 and fit_tau positive");
   PD_TRY(transform_enqueue(ctx, out->D1, W, H, p->model_order, p->delta_dt, out->fitted,
-                           out->D2, ctx->ws));
+                           out->D2, ctx->ws, p->fit_iters, p->fit_tau));
   mark(ctx, rec, 4);
   if (times) cudaEventRecord(ctx->ev[2], s);
   launch_slic(s, out->D2, W, H, p->slic_K, p->slic_m, p->slic_iters, out->labels, out->D3,

@@ -158,7 +158,9 @@ struct RoadCoefF {
   float c, s, a0, a1, a2, uc, vc, pad;
 };
 size_t moments_scratch_bytes(int W, int H);
-void launch_moments(cudaStream_t s, const float* D1, int W, int H, void* scratch, int64_t* sums);
+// fit != nullptr: only the inliers |D1 - f| <= tau of that fit count (the robust refit).
+void launch_moments(cudaStream_t s, const float* D1, int W, int H, void* scratch, int64_t* sums,
+                    const RoadCoefF* fit = nullptr, float tau = 0.0f);
 size_t roll_scratch_bytes();
 // Returns the number of kernels launched.
 int launch_roll_solve(cudaStream_t s, const int64_t* sums, int order, int W, int H,

@@ -26,11 +26,25 @@ __device__ __forceinline__ long long warp_sum_ll(long long x) {
   return x;
 }
 
+// The road model of a fit at pixel (u, v), in single precision in the operation order of the
+// model definition (no FMA): the value the transform subtracts.
+__device__ __forceinline__ float road_f32(const RoadCoefF& c, int u, int v) {
+  const float t1 = ((float)v - c.vc) * c.c;
+  const float t2 = ((float)u - c.uc) * c.s;
+  const float vp = (t1 - t2) + c.vc;
+  return (c.a0 + c.a1 * vp) + c.a2 * (vp * vp);
+}
+
 // Per-block int64 partial sums: count, sum u~^i v~^j (i + j <= 4), sum q u~^i v~^j (i + j <= 2),
-// sum q^2 with q = rint(1024 D1), u~ = 2u - (W-1), v~ = 2v - (H-1), over pixels with D1 >= 0.
+// sum q^2 with q = rint(1024 D1), u~ = 2u - (W-1), v~ = 2v - (H-1), over pixels with D1 >= 0 and,
+// when fit is given, |D1 - f(p)| <= tau (the inliers of that fit).
 __global__ void __launch_bounds__(kMomThreads) k_moments_partial(const float* __restrict__ D1,
                                                                  int W, int H,
-                                                                 long long* __restrict__ partial) {
+                                                                 long long* __restrict__ partial,
+                                                                 const RoadCoefF* __restrict__ fit,
+                                                                 float tau) {
+  RoadCoefF cf;
+  if (fit) cf = *fit;
   long long acc[kNumSums];
 #pragma unroll
   for (int i = 0; i < kNumSums; ++i) acc[i] = 0;
@@ -40,8 +54,9 @@ __global__ void __launch_bounds__(kMomThreads) k_moments_partial(const float* __
   for (size_t p = start + threadIdx.x; p < end; p += kMomThreads) {
     float d = D1[p];
     if (!(d >= 0.0f)) continue;
-    long long q = __float2ll_rn(d * 1024.0f);  // exact scaling; rounds half to even like rint
     int u = (int)(p % W), v = (int)(p / W);
+    if (fit && !(fabsf(d - road_f32(cf, u, v)) <= tau)) continue;
+    long long q = __float2ll_rn(d * 1024.0f);  // exact scaling; rounds half to even like rint
     long long ut = 2LL * u - (W - 1), vt = 2LL * v - (H - 1);
     long long up[5], vp[5];
     up[0] = vp[0] = 1;
@@ -400,13 +415,21 @@ __global__ void __launch_bounds__(kRollWarp) k_roll_final(const int64_t* __restr
   double k = 2.0 / sc;
   double vc = (double)(H - 1) * 0.5;
   double b0 = beta[0], b1 = beta[1], b2 = order == 2 ? beta[2] : 0.0;
-  pd_road_model out;
+  pd_road_model out{};  // zero-initialised: the padding after `order` is written as zeros
   out.order = order;
   out.roll = phi;
   out.a[2] = b2 * k * k;
   out.a[1] = b1 * k - 2.0 * b2 * k * k * vc;
   out.a[0] = b0 - b1 * k * vc + b2 * k * k * vc * vc;
-  if (fitted) *fitted = out;
+  if (fitted) {  // written as whole words, so the padding after `order` is defined (zero)
+    static_assert(sizeof(pd_road_model) == 40, "pd_road_model layout");
+    unsigned long long* w = reinterpret_cast<unsigned long long*>(fitted);
+    w[0] = (unsigned long long)(unsigned int)out.order;
+    w[1] = (unsigned long long)__double_as_longlong(out.a[0]);
+    w[2] = (unsigned long long)__double_as_longlong(out.a[1]);
+    w[3] = (unsigned long long)__double_as_longlong(out.a[2]);
+    w[4] = (unsigned long long)__double_as_longlong(out.roll);
+  }
   RoadCoefF cf;
   cf.c = (float)cos(phi);
   cf.s = (float)sin(phi);
@@ -430,10 +453,7 @@ __global__ void k_d2(const float* __restrict__ D1, int W, int H, const RoadCoefF
   float d1 = D1[p];
   float out = delta_dt;
   if (d1 >= 0.0f) {
-    float t1 = ((float)v - c.vc) * c.c;
-    float t2 = ((float)u - c.uc) * c.s;
-    float vp = (t1 - t2) + c.vc;
-    float f = (c.a0 + c.a1 * vp) + c.a2 * (vp * vp);
+    const float f = road_f32(c, u, v);
     out = (d1 - f) + delta_dt;
     if (out < 0.0f) out = 0.0f;
   }
@@ -451,10 +471,11 @@ size_t roll_scratch_bytes() {
   return (size_t)(kGridBlocks + kRefineRounds * kRoundBlocks) * sizeof(RollBest);
 }
 
-void launch_moments(cudaStream_t s, const float* D1, int W, int H, void* scratch, int64_t* sums) {
+void launch_moments(cudaStream_t s, const float* D1, int W, int H, void* scratch, int64_t* sums,
+                    const RoadCoefF* fit, float tau) {
   int nblocks = (int)(((size_t)W * H + kMomPixPerBlock - 1) / kMomPixPerBlock);
   long long* partial = static_cast<long long*>(scratch);
-  k_moments_partial<<<nblocks, kMomThreads, 0, s>>>(D1, W, H, partial);
+  k_moments_partial<<<nblocks, kMomThreads, 0, s>>>(D1, W, H, partial, fit, tau);
   k_moments_final<<<1, kNumSums * 32, 0, s>>>(partial, nblocks, sums);
 }
 
@@ -500,6 +521,7 @@ extern "C" pd_status pd_transform_noalloc(const float* D1, int W, int H, int ord
   if ((long long)W * (long long)H > kNoAllocMaxPixels) return PD_ERR_INVALID_ARG;
   if (order != 1 && order != 2) return PD_ERR_INVALID_ARG;
   if (!isfinite(delta_dt)) return PD_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(fitted) & 7u) return PD_ERR_INVALID_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
