@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <vector>
 
 #include "batch.cuh"
@@ -32,6 +33,19 @@ pd_status cuda_ok(pd_ctx* c, cudaError_t e, const char* what) {
     return fail(c, PD_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
   }
   return fail(c, PD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void raise_smem_limit(const void* f, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> set;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = set[{f, dev}];
+  if (bytes <= cur) return;
+  if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+      cudaSuccess)
+    cur = bytes;
 }
 
 pd_status launched(pd_ctx* c, const char* what) { return cuda_ok(c, cudaGetLastError(), what); }
@@ -838,7 +852,7 @@ pd_status pd_superpixels(pd_ctx* ctx, const float* D2, int W, int H, int K, floa
   slic_grid(W, H, K, &nx, &ny);
   if (n_centres) *n_centres = nx * ny;
   PD_TRY(ensure_ws(ctx, slic_scratch_bytes(nx * ny)));
-  launch_slic(ctx->stream, D2, W, H, K, m, iters, labels, D3, centres, ctx->ws);
+  count_launches(ctx, launch_slic(ctx->stream, D2, W, H, K, m, iters, labels, D3, centres, ctx->ws));
   return launched(ctx, "pd_superpixels");
 }
 
@@ -851,7 +865,8 @@ pd_status pd_pothole_mask(pd_ctx* ctx, const float* D2, const float* D1, const f
   PD_REQUIRE(mode == 0 || mode == 1, "mode %d must be 0 or 1", mode);
   PD_REQUIRE(isfinite(delta_pd), "delta_pd must be finite");
   PD_TRY(ensure_ws(ctx, threshold_scratch_bytes()));
-  launch_threshold(ctx->stream, D2, D1, D3, W, H, delta_pd, mode, mask, thresholds, E2, ctx->ws);
+  count_launches(ctx, launch_threshold(ctx->stream, D2, D1, D3, W, H, delta_pd, mode, mask,
+                                       thresholds, E2, ctx->ws));
   return launched(ctx, "pd_pothole_mask");
 }
 
@@ -960,14 +975,13 @@ pd_status pipeline_impl(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, 
                            out->D2, ctx->ws, p->fit_iters, p->fit_tau));
   mark(ctx, rec, 4);
   if (times) cudaEventRecord(ctx->ev[2], s);
-  launch_slic(s, out->D2, W, H, p->slic_K, p->slic_m, p->slic_iters, out->labels, out->D3,
-              nullptr, ctx->ws);
-  count_launches(ctx, 3 + 2 * (p->slic_iters > 0 ? p->slic_iters : 1));
+  count_launches(ctx, launch_slic(s, out->D2, W, H, p->slic_K, p->slic_m, p->slic_iters,
+                                  out->labels, out->D3, nullptr, ctx->ws));
   mark(ctx, rec, 5);
   if (times) cudaEventRecord(ctx->ev[3], s);
-  launch_threshold(s, out->D2, out->D1, out->D3, W, H, p->delta_pd, p->threshold_mode, out->mask,
-                   out->thresholds, nullptr, ctx->ws);
-  count_launches(ctx, 3);
+  count_launches(ctx, launch_threshold(s, out->D2, out->D1, out->D3, W, H, p->delta_pd,
+                                       p->threshold_mode, out->mask, out->thresholds, nullptr,
+                                       ctx->ws));
   if (ccl)
     count_launches(ctx, launch_ccl(s, out->mask, out->labels, W, H, conn, out->components,
                                    out->comps, max_comps, out->n_comps, ctx->ws));

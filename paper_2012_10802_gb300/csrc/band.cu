@@ -536,12 +536,7 @@ void launch_compact(cudaStream_t s, dim3 grid, const uint8_t* cost_il, uint8_t* 
   const int nsm = ntiles <= kMaxSmemTiles ? ntiles : 0;
   const size_t ring = (size_t)kCWarps * kCStages * NSM * 32 * sizeof(uint4);
   const size_t smem = ring + (((size_t)nsm * sizeof(int16_t) + 15) & ~size_t(15));
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_aggregate_band<GL, NSM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(ring + kMaxSmemTiles * sizeof(int16_t)));
-    attr_set = true;
-  }
+  raise_smem_limit((const void*)k_aggregate_band<GL, NSM>, smem);
   k_aggregate_band<GL, NSM><<<grid, kCWarps * 32, smem, s>>>(cost_il, out, W, H, D, packed, P1x2,
                                                              K21x2, vol_bytes, band, nsm,
                                                              (size_t)W * H * 16);
@@ -579,12 +574,7 @@ void launch_wta_band(cudaStream_t s, const uint8_t* vols, int ndirs, size_t vol_
                      uint32_t* rkeys) {
   const size_t smem = (size_t)kWtaBandPix * D * sizeof(uint16_t) +
                       (size_t)(kWtaBandPix + D - 1) * sizeof(uint32_t);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_wta_band, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)((size_t)kWtaBandPix * kMaxD * 2 + (kWtaBandPix + kMaxD) * 4));
-    attr_set = true;
-  }
+  raise_smem_limit((const void*)k_wta_band, smem);
   k_wta_band<<<dim3((W + kWtaBandPix - 1) / kWtaBandPix, H), 2 * kWtaBandPix, smem, s>>>(
       vols, ndirs, vol_bytes, W, D, band, (size_t)W * H * 16, d_int, dsub, rkeys);
 }

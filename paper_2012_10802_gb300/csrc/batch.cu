@@ -160,11 +160,7 @@ void launch_batch_wave(cudaStream_t s, const BatchWaveDev& w, int P1, int P2, in
   k_cost_b<<<w.total[kStageCost], kCostThreads, 0, s>>>(w.pairs, w.starts[kStageCost], n);
   cudaMemsetAsync(w.counter, 0, sizeof(unsigned int), s);
   const size_t smem = batch_agg_smem(agg_warps);
-  static size_t smem_set = 0;
-  if (smem > smem_set) {
-    cudaFuncSetAttribute(k_aggregate_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    smem_set = smem;
-  }
+  raise_smem_limit((const void*)k_aggregate_b, smem);
   k_aggregate_b<<<agg_blocks, agg_warps * 32, smem, s>>>(w.pairs, w.segs, w.nseg, w.ntasks,
                                                          w.counter, P1x2, K21x2);
   k_wta_b<<<w.total[kStageWta], kWtaThreads, 4096 * sizeof(uint16_t), s>>>(
@@ -177,14 +173,13 @@ void launch_batch_aggregate_only(cudaStream_t s, const BatchWaveDev& w, int P1, 
   const uint32_t P1x2 = (uint32_t)P1 * 0x10001u, K21x2 = (uint32_t)(P2 - P1) * 0x10001u;
   cudaMemsetAsync(w.counter, 0, sizeof(unsigned int), s);
   const size_t smem = batch_agg_smem(agg_warps);
-  cudaFuncSetAttribute(k_aggregate_b, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit((const void*)k_aggregate_b, smem);
   k_aggregate_b<<<agg_blocks, agg_warps * 32, smem, s>>>(w.pairs, w.segs, w.nseg, w.ntasks,
                                                          w.counter, P1x2, K21x2);
 }
 
 int batch_max_blocks_per_sm(int agg_warps) {
-  cudaFuncSetAttribute(k_aggregate_b, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)batch_agg_smem(agg_warps));
+  raise_smem_limit((const void*)k_aggregate_b, batch_agg_smem(agg_warps));
   int n = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_aggregate_b, agg_warps * 32,
                                                 batch_agg_smem(agg_warps));

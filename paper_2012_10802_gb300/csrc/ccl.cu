@@ -51,10 +51,32 @@ __device__ __forceinline__ void merge(int32_t* L, int a, int b, int* err) {
   atomicExch(err, 1);
 }
 
+// Running statistics of one component (atomics from the statistics pass).
+struct CompAcc {
+  int count, umin, vmin, umax, vmax, sp_first, multi, pad;
+  unsigned long long sum_u, sum_v;
+};
+
+__device__ void acc_init_one(CompAcc* out) {
+  CompAcc a;
+  a.count = 0;
+  a.umin = INT_MAX;
+  a.vmin = INT_MAX;
+  a.umax = -1;
+  a.vmax = -1;
+  a.sp_first = INT_MIN;
+  a.multi = 0;
+  a.pad = 0;
+  a.sum_u = 0;
+  a.sum_v = 0;
+  *out = a;
+}
+
 // Labels inside one 16 x 16 tile, in shared memory: the same union-find on tile-local indices
 // (local raster order within a tile agrees with the global raster order of its pixels), then
 // every mask pixel gets the global raster index of its tile-local root.  Block 0 also clears the
-// flags (component total and error) for the later kernels.
+// flags (component total and error) and, spread over all blocks, the component statistics for the
+// later kernels.
 constexpr int kTile = 16;
 
 __device__ __forceinline__ int find_local(const int* s, int x) {
@@ -85,7 +107,9 @@ __device__ __forceinline__ void merge_local(int* s, int a, int b) {
 
 __global__ void __launch_bounds__(kTile * kTile) k_ccl_local(const uint8_t* __restrict__ mask,
                                                              int W, int H, int conn,
-                                                             int32_t* __restrict__ L, int* flags) {
+                                                             int32_t* __restrict__ L, int* flags,
+                                                             CompAcc* __restrict__ acc,
+                                                             int max_comps) {
   __shared__ int s[kTile * kTile];
   const int tx = threadIdx.x % kTile, ty = threadIdx.x / kTile;
   const int u = blockIdx.x * kTile + tx, v = blockIdx.y * kTile + ty;
@@ -94,6 +118,12 @@ __global__ void __launch_bounds__(kTile * kTile) k_ccl_local(const uint8_t* __re
   const int me = threadIdx.x;
   s[me] = m ? me : -1;
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < 2) flags[threadIdx.x] = 0;
+  {
+    const int nthreads = gridDim.x * gridDim.y * kTile * kTile;
+    for (int k = (blockIdx.y * gridDim.x + blockIdx.x) * kTile * kTile + threadIdx.x;
+         k < max_comps; k += nthreads)
+      acc_init_one(acc + k);
+  }
   __syncthreads();
   if (m) {
     if (tx > 0 && s[me - 1] >= 0) merge_local(s, me, me - 1);
@@ -151,31 +181,9 @@ __global__ void __launch_bounds__(kCclThreads) k_ccl_flatten_count(int32_t* L, i
 }
 
 // Exclusive scan of the block counts in one block; total number of components in *total.
-struct CompAcc {
-  int count, umin, vmin, umax, vmax, sp_first, multi, pad;
-  unsigned long long sum_u, sum_v;
-};
-
-__device__ void acc_init_one(CompAcc* out) {
-  CompAcc a;
-  a.count = 0;
-  a.umin = INT_MAX;
-  a.vmin = INT_MAX;
-  a.umax = -1;
-  a.vmax = -1;
-  a.sp_first = INT_MIN;
-  a.multi = 0;
-  a.pad = 0;
-  a.sum_u = 0;
-  a.sum_v = 0;
-  *out = a;
-}
-
 __global__ void __launch_bounds__(kCclThreads) k_ccl_scan(const int* __restrict__ counts, int nb,
                                                           int* __restrict__ offsets,
-                                                          int* __restrict__ total, CompAcc* acc,
-                                                          int max_comps) {
-  for (int k = threadIdx.x; k < max_comps; k += kCclThreads) acc_init_one(acc + k);
+                                                          int* __restrict__ total) {
   __shared__ int warp_sums[32];
   __shared__ int carry;
   if (threadIdx.x == 0) carry = 0;
@@ -237,28 +245,45 @@ __global__ void __launch_bounds__(kCclThreads) k_ccl_ids(const int32_t* __restri
 __global__ void k_ccl_stats(const int32_t* __restrict__ L, const int32_t* __restrict__ cid,
                             const int32_t* __restrict__ sp, int W, int H,
                             int32_t* __restrict__ labels, CompAcc* acc, int max_comps) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= W * H) return;
-  const int r = L[p];
-  if (r < 0) {
-    labels[p] = -1;
-    return;
+  const unsigned FULL = 0xffffffffu;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
+  int k = -1;
+  if (p < W * H) {
+    const int r = L[p];
+    k = r < 0 ? -1 : cid[r];
+    labels[p] = k;
   }
-  const int k = cid[r];
-  labels[p] = k;
-  if (k >= max_comps) return;
-  const int u = p % W, v = p / W;
-  CompAcc* a = acc + k;
-  atomicAdd(&a->count, 1);
-  atomicMin(&a->umin, u);
-  atomicMin(&a->vmin, v);
-  atomicMax(&a->umax, u);
-  atomicMax(&a->vmax, v);
-  atomicAdd(&a->sum_u, (unsigned long long)u);
-  atomicAdd(&a->sum_v, (unsigned long long)v);
-  const int s = sp[p];
-  const int old = atomicCAS(&a->sp_first, INT_MIN, s);
-  if (old != INT_MIN && old != s) a->multi = 1;
+  // the lanes of a warp that share a component add their pixels in one set of atomics
+  const bool valid = k >= 0 && k < max_comps;
+  const int u = valid ? p % W : 0, v = valid ? p / W : 0, s = valid ? sp[p] : 0;
+  unsigned pending = __ballot_sync(FULL, valid);
+  while (pending) {
+    const int leader = __ffs(pending) - 1;
+    const int kl = __shfl_sync(FULL, k, leader);
+    const bool mine = valid && k == kl;
+    const unsigned peers = __ballot_sync(FULL, mine);
+    const int umin = __reduce_min_sync(FULL, mine ? u : INT_MAX);
+    const int umax = __reduce_max_sync(FULL, mine ? u : -1);
+    const int vmin = __reduce_min_sync(FULL, mine ? v : INT_MAX);
+    const int vmax = __reduce_max_sync(FULL, mine ? v : -1);
+    const unsigned su = __reduce_add_sync(FULL, mine ? (unsigned)u : 0u);  // < 32 * 4096
+    const unsigned sv = __reduce_add_sync(FULL, mine ? (unsigned)v : 0u);
+    const int smin = __reduce_min_sync(FULL, mine ? s : INT_MAX);
+    const int smax = __reduce_max_sync(FULL, mine ? s : INT_MIN);
+    if (lane == leader) {
+      CompAcc* a = acc + kl;
+      atomicAdd(&a->count, __popc(peers));
+      atomicMin(&a->umin, umin);
+      atomicMin(&a->vmin, vmin);
+      atomicMax(&a->umax, umax);
+      atomicMax(&a->vmax, vmax);
+      atomicAdd(&a->sum_u, (unsigned long long)su);
+      atomicAdd(&a->sum_v, (unsigned long long)sv);
+      const int old = atomicCAS(&a->sp_first, INT_MIN, smin);
+      if (smin != smax || (old != INT_MIN && old != smin)) a->multi = 1;
+    }
+    pending &= ~peers;
+  }
 }
 
 // Statistics and the fake-pothole rule: the centroid lies in a corner cell of the image split
@@ -319,10 +344,10 @@ int launch_ccl(cudaStream_t s, const uint8_t* mask, const int32_t* sp, int W, in
   CompAcc* acc = c.take<CompAcc>(max_comps);
   const int T = 256, G = (n + T - 1) / T;
   const dim3 tiles((W + kTile - 1) / kTile, (H + kTile - 1) / kTile);
-  k_ccl_local<<<tiles, kTile * kTile, 0, s>>>(mask, W, H, conn, L, flags);
+  k_ccl_local<<<tiles, kTile * kTile, 0, s>>>(mask, W, H, conn, L, flags, acc, max_comps);
   k_ccl_border<<<tiles, kTile * kTile, 0, s>>>(mask, W, H, conn, L, flags + 1);
   k_ccl_flatten_count<<<nb, kCclThreads, 0, s>>>(L, n, flags + 1, counts);
-  k_ccl_scan<<<1, kCclThreads, 0, s>>>(counts, nb, offsets, flags, acc, max_comps);
+  k_ccl_scan<<<1, kCclThreads, 0, s>>>(counts, nb, offsets, flags);
   k_ccl_ids<<<nb, kCclThreads, 0, s>>>(L, n, offsets, cid, root_of, max_comps);
   k_ccl_stats<<<G, T, 0, s>>>(L, cid, sp, W, H, labels, acc, max_comps);
   const int GK = (max_comps + T - 1) / T;

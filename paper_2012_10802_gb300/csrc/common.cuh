@@ -71,6 +71,11 @@ inline size_t carve_size(size_t& acc, size_t n) {
   return acc;
 }
 
+// Raises kernel f's dynamic shared-memory limit to at least `bytes` on the current device.  The
+// limit belongs to the device's context, so it is tracked per (kernel, device); repeated calls
+// cost a lookup.
+void raise_smem_limit(const void* f, size_t bytes);
+
 // Aggregation directions (dx, dy): the first 4 are the axis paths, the last 4 the diagonals.
 struct DirSet {
   int n;
@@ -171,12 +176,14 @@ void launch_d2(cudaStream_t s, const float* D1, int W, int H, const RoadCoefF* c
 // ------------------------------------------------------ superpixel / mask (detect.cu)
 void slic_grid(int W, int H, int K, int* nx, int* ny);
 size_t slic_scratch_bytes(int n_centres);
-// Runs seeds + `iters` rounds of assignment/update; writes labels and D3.
-void launch_slic(cudaStream_t s, const float* D2, int W, int H, int K, float m, int iters,
-                 int32_t* labels, float* D3, float* centres_out, void* scratch);
+// Runs seeds + `iters` rounds of assignment/update; writes labels and D3.  Returns the number
+// of kernels it launched.
+int launch_slic(cudaStream_t s, const float* D2, int W, int H, int K, float m, int iters,
+                int32_t* labels, float* D3, float* centres_out, void* scratch);
 size_t threshold_scratch_bytes();
-void launch_threshold(cudaStream_t s, const float* D2, const float* D1, const float* D3, int W,
-                      int H, float delta_pd, int mode, uint8_t* mask, double* thresholds,
-                      double* E2, void* scratch);
+// Returns the number of kernels it launched.
+int launch_threshold(cudaStream_t s, const float* D2, const float* D1, const float* D3, int W,
+                     int H, float delta_pd, int mode, uint8_t* mask, double* thresholds,
+                     double* E2, void* scratch);
 
 }  // namespace pd

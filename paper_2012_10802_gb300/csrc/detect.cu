@@ -107,46 +107,66 @@ __global__ void __launch_bounds__(kTileThreads) k_slic_assign(
   if (tid == 0) ncand = 0;
   __syncthreads();
   if (do_assign) {
-    // conservative box test (1 px margin); the exact test runs per pixel below
+    // conservative box test (1 px margin); the exact test runs per pixel below.  Thread t tests
+    // centres 4t .. 4t+3 of each chunk of 4 * kTileThreads, and a block scan of the per-thread
+    // counts places the hits, so the list stays in index order.
     const float bx0 = (float)x0 - 1.0f, bx1 = (float)(x0 + kTile), by0 = (float)y0 - 1.0f,
                 by1 = (float)(y0 + kTile);
-    constexpr int kBatch = 4;  // centres per thread loaded together before the ordered scan
-    for (int base0 = 0; base0 < n; base0 += kBatch * kTileThreads) {
-      float bx[kBatch], byy[kBatch];
+    for (int base = 0; base < n; base += 4 * kTileThreads) {  // block-uniform
+      const int k0 = base + 4 * tid;
+      float fx[4], fy[4], fv[4];
+      if (k0 + 4 <= n) {  // 16-byte aligned: the arrays start on 256-byte boundaries
+        const float4 X = *reinterpret_cast<const float4*>(cx + k0);
+        const float4 Y = *reinterpret_cast<const float4*>(cy + k0);
+        const float4 V = *reinterpret_cast<const float4*>(cv + k0);
+        fx[0] = X.x, fx[1] = X.y, fx[2] = X.z, fx[3] = X.w;
+        fy[0] = Y.x, fy[1] = Y.y, fy[2] = Y.z, fy[3] = Y.w;
+        fv[0] = V.x, fv[1] = V.y, fv[2] = V.z, fv[3] = V.w;
+      } else {
 #pragma unroll
-      for (int b = 0; b < kBatch; ++b) {
-        int k = base0 + b * kTileThreads + tid;
-        bx[b] = k < n ? cx[k] : 0.f;
-        byy[b] = k < n ? cy[k] : 0.f;
+        for (int b = 0; b < 4; ++b) {
+          const bool in = k0 + b < n;
+          fx[b] = in ? cx[k0 + b] : 0.0f;
+          fy[b] = in ? cy[k0 + b] : 0.0f;
+          fv[b] = in ? cv[k0 + b] : 0.0f;
+        }
       }
+      bool q[4];
+      int cnt = 0;
 #pragma unroll
-      for (int b = 0; b < kBatch; ++b) {
-        const int base = base0 + b * kTileThreads;
-        if (base >= n) break;  // block-uniform
-        const int k = base + tid;
-        const float fx = bx[b], fy = byy[b];
-        const bool q =
-            k < n && (fx + Sf >= bx0) && (fx - Sf <= bx1) && (fy + Sf >= by0) && (fy - Sf <= by1);
-        const unsigned bal = __ballot_sync(0xffffffffu, q);
-        if (lane == 0) wcount[warp] = __popc(bal);
-        __syncthreads();
-        int off = ncand;
-        for (int w = 0; w < warp; ++w) off += wcount[w];
-        const int pos = off + __popc(bal & ((1u << lane) - 1u));
-        if (q && pos < kCandCap) {
-          cand[pos] = k;
-          ccx[pos] = fx;
-          ccy[pos] = fy;
-          ccv[pos] = cv[k];
-        }
-        __syncthreads();
-        if (tid == 0) {
-          int tot = ncand;
-          for (int w = 0; w < kTileThreads / 32; ++w) tot += wcount[w];
-          ncand = tot;
-        }
-        __syncthreads();
+      for (int b = 0; b < 4; ++b) {
+        q[b] = k0 + b < n && (fx[b] + Sf >= bx0) && (fx[b] - Sf <= bx1) && (fy[b] + Sf >= by0) &&
+               (fy[b] - Sf <= by1);
+        cnt += q[b] ? 1 : 0;
       }
+      int incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      if (lane == 31) wcount[warp] = incl;
+      __syncthreads();
+      int pos = ncand + incl - cnt;
+      for (int w = 0; w < warp; ++w) pos += wcount[w];
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        if (q[b]) {
+          if (pos < kCandCap) {
+            cand[pos] = k0 + b;
+            ccx[pos] = fx[b];
+            ccy[pos] = fy[b];
+            ccv[pos] = fv[b];
+          }
+          ++pos;
+        }
+      __syncthreads();
+      if (tid == 0) {
+        int tot = ncand;
+        for (int w = 0; w < kTileThreads / 32; ++w) tot += wcount[w];
+        ncand = tot;
+      }
+      __syncthreads();
     }
   }
   const int nc = ncand;
@@ -213,9 +233,11 @@ __global__ void __launch_bounds__(kTileThreads) k_slic_assign(
       atomicAdd(a + 2, sacc[i][2]);
       atomicAdd(a + 3, sacc[i][3]);
     }
+
 }
 
-// Centre update from the exact sums (empty clusters keep their centre); clears the sums.
+// Centre update from the exact sums (empty clusters keep their centre); clears the sums.  It is
+// a separate launch over many SMs because the three double divisions per centre are slow on one.
 __global__ void k_slic_update(int n, unsigned long long* __restrict__ acc, float* __restrict__ cx,
                               float* __restrict__ cy, float* __restrict__ cv) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -438,8 +460,8 @@ size_t slic_scratch_bytes(int n) {
   return acc;
 }
 
-void launch_slic(cudaStream_t s, const float* D2, int W, int H, int K, float m, int iters,
-                 int32_t* labels, float* D3, float* centres_out, void* scratch) {
+int launch_slic(cudaStream_t s, const float* D2, int W, int H, int K, float m, int iters,
+                int32_t* labels, float* D3, float* centres_out, void* scratch) {
   int nx, ny;
   slic_grid(W, H, K, &nx, &ny);
   int n = nx * ny;
@@ -463,6 +485,7 @@ void launch_slic(cudaStream_t s, const float* D2, int W, int H, int K, float m, 
   size_t N = (size_t)W * H;
   k_slic_d3<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(labels, cv, N, D3);
   if (centres_out) k_centres_out<<<(n + 127) / 128, 128, 0, s>>>(n, cx, cy, cv, centres_out);
+  return 3 + 2 * rounds + (centres_out ? 1 : 0);
 }
 
 size_t threshold_scratch_bytes() {
@@ -472,21 +495,24 @@ size_t threshold_scratch_bytes() {
   return acc;
 }
 
-void launch_threshold(cudaStream_t s, const float* D2, const float* D1, const float* D3, int W,
-                      int H, float delta_pd, int mode, uint8_t* mask, double* thresholds,
-                      double* E2, void* scratch) {
+int launch_threshold(cudaStream_t s, const float* D2, const float* D1, const float* D3, int W,
+                     int H, float delta_pd, int mode, uint8_t* mask, double* thresholds,
+                     double* E2, void* scratch) {
   Carve c(scratch);
   unsigned long long* hist = c.take<unsigned long long>(2 * kBins * 4);
   double* thr = c.take<double>(2);
   if (thresholds) thr = thresholds;
   cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * 2 * kBins * 4, s);
+  // about 8 resident blocks per SM: each warp's per-bin loop is a latency chain, so the kernel
+  // needs many of them in flight
   const int xb = (W + 255) / 256;
-  int yb = (2 * 152 + xb - 1) / xb;
+  int yb = (8 * 152 + xb - 1) / xb;
   yb = yb < H ? yb : H;
   k_thresh_hist<<<dim3(xb, yb), 256, 0, s>>>(D2, D1, W, H, hist);
   k_thresh_solve<<<1, kSolveThreads, 0, s>>>(hist, delta_pd, mode, thr, E2);
   size_t N = (size_t)W * H;
   k_mask<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(D3, N, thr, mask);
+  return 3;
 }
 
 }  // namespace pd

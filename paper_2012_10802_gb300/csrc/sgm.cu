@@ -251,14 +251,10 @@ void launch_aggregate(cudaStream_t s, const uint8_t* cost_il, int W, int H, int 
   int lines_per_block = kAggWarps * (32 / G);
   dim3 grid((maxlines + lines_per_block - 1) / lines_per_block, dirs.n);
   const size_t smem = (size_t)kAggWarps * kStages * 32 * sizeof(uint4);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_aggregate<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_aggregate<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_aggregate<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_aggregate<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr_set = true;
-  }
+  raise_smem_limit((const void*)k_aggregate<2>, smem);
+  raise_smem_limit((const void*)k_aggregate<4>, smem);
+  raise_smem_limit((const void*)k_aggregate<8>, smem);
+  raise_smem_limit((const void*)k_aggregate<16>, smem);
   uint32_t P1x2 = (uint32_t)P1 * 0x10001u;
   uint32_t K21x2 = (uint32_t)(P2 - P1) * 0x10001u;
   uint32_t packed = 0;

@@ -194,7 +194,7 @@ def _D2(orc, W, H, D, seed):
 
 
 @pytest.mark.parametrize("W,H,K,iters", [(320, 240, 1000, 10), (97, 61, 40, 3), (320, 240, 60, 0),
-                                         (200, 150, 5, 4)])
+                                         (200, 150, 5, 4), (64, 48, 1500, 2)])
 def test_superpixels_parity(orc, B, ctx, W, H, K, iters):
     _, D2 = _D2(orc, W, H, 32, 31)
     lab_o, cen_o = orc.slic(D2, K, 10.0, iters)
@@ -224,6 +224,30 @@ def test_pothole_mask_parity(orc, B, ctx, mode, W, H):
     assert np.array_equal(np.isnan(e), np.isnan(E2_o))
     assert np.array_equal(e[~np.isnan(e)], E2_o[~np.isnan(E2_o)])
     assert np.array_equal(host(mask), orc.mask(D3, t_s))
+
+
+@pytest.mark.parametrize("W,H", [(3, 3), (2, 40), (40, 2), (31, 17), (32, 10), (61, 66),
+                                 (1280, 9)])
+def test_pothole_mask_ragged_and_invalid(orc, B, ctx, W, H):
+    """Sizes around the histogram's 30-column strips and 8-row chunks (and below the 3x3 window),
+    a sloped map with a dip, and 4 % of the pixels without a disparity (D1 < 0)."""
+    rng = np.random.default_rng(W * 1000 + H)
+    v = np.arange(H, dtype=np.float32)[:, None]
+    D2 = (12.0 + 0.05 * v + rng.normal(0.0, 0.3, (H, W))).astype(np.float32)
+    D2[H // 3: H // 3 + 3, W // 4: W // 4 + 5] -= 4.0
+    D1 = np.where(rng.random((H, W)) < 0.04, -1.0, 1.0).astype(np.float32)
+    rc, t_r, t_s, E2_o = orc.threshold(D2, D1, 2.36, 0)
+    E2 = torch.empty(256, dtype=torch.float64, device="cuda")
+    mask, thr = B.pd_pothole_mask(ctx, dev(D2), dev(D1), dev(D2), 2.36, 0, E2=E2)
+    t = host(thr)
+    e = host(E2)
+    assert np.array_equal(np.isnan(e), np.isnan(E2_o))
+    assert np.array_equal(e[~np.isnan(e)], E2_o[~np.isnan(E2_o)])
+    if rc == 0:
+        assert t[0] == t_r and t[1] == t_s
+    else:
+        assert np.isnan(t[0]) and t[1] == -np.inf
+    assert np.array_equal(host(mask), orc.mask(D2, t[1]))
 
 
 def test_pothole_mask_empty_split(orc, B, ctx):
