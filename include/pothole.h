@@ -255,7 +255,8 @@ pd_status pd_transform_noalloc(const float* D1, int W, int H, int order, float d
  * (D2 - value)^2 + ((x - cx)^2 + (y - cy)^2) (m / S)^2, lower index on ties) and mean update.
  * Then D3 (Sec. II-E): every pixel gets the mean D2 of its superpixel.
  * labels: int32 [H][W]; D3: float [H][W]; centres (may be NULL): float [nx*ny][3].
- * Returns the centre count in *n_centres (host, may be NULL). */
+ * Returns the centre count in *n_centres (host, may be NULL).
+ * Centre means use exact integer sums of rint(1024 D2); they are exact for |D2| < 2^27 px. */
 pd_status pd_superpixels(pd_ctx* ctx, const float* D2, int W, int H, int K, float m, int iters,
                          int32_t* labels, float* D3, float* centres, int* n_centres);
 

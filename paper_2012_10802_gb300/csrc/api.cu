@@ -206,8 +206,7 @@ pd_status sgm_enqueue(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, in
   else
     launch_kappa(s, W, H, model->order, model->a, cos(model->roll), sin(model->roll),
                  (double)p->delta_pt, kap);
-  launch_census(s, left, W, H, pitch, nullptr, sc.cl);
-  launch_census(s, right, W, H, pitch, kap, sc.cr);
+  launch_census_pair(s, left, right, W, H, pitch, kap, sc.cl, sc.cr);
   launch_cost(s, sc.cl, sc.cr, W, H, p->D, 1, sc.cost);
   cudaMemsetAsync(sc.rkeys, 0xff, N * sizeof(uint32_t), s);
   mark(ctx, rec, 1);
@@ -216,7 +215,7 @@ pd_status sgm_enqueue(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, in
   launch_wta(s, sc.vols, p->paths, vol, nullptr, W, H, p->D, d_int, sc.dsub, sc.rkeys);
   launch_lr(s, d_int, sc.dsub, sc.rkeys, kap, W, H, p->D, p->lr_tol, D1);
   mark(ctx, rec, 3);
-  count_launches(ctx, 7);
+  count_launches(ctx, 6);
   return launched(ctx, "pd_sgm");
 }
 
@@ -233,8 +232,7 @@ pd_status sgm_band_enqueue(pd_ctx* ctx, const uint8_t* left, const uint8_t* righ
   mark(ctx, rec, 0);
   launch_kappa(s, W, H, model->order, model->a, cos(model->roll), sin(model->roll),
                (double)p->delta_pt, kap);
-  launch_census(s, left, W, H, pitch, nullptr, sc.cl);
-  launch_census(s, right, W, H, pitch, kap, sc.cr);
+  launch_census_pair(s, left, right, W, H, pitch, kap, sc.cl, sc.cr);
   launch_cost_band(s, sc.cl, sc.cr, W, H, p->D, band, sc.cost);
   cudaMemsetAsync(sc.rkeys, 0xff, N * sizeof(uint32_t), s);
   mark(ctx, rec, 1);
@@ -244,7 +242,7 @@ pd_status sgm_band_enqueue(pd_ctx* ctx, const uint8_t* left, const uint8_t* righ
   launch_wta_band(s, sc.vols, p->paths, vol, W, H, p->D, band, d_int, sc.dsub, sc.rkeys);
   launch_lr_band(s, d_int, sc.dsub, sc.rkeys, kap, W, H, p->D, band, p->lr_tol, D1);
   mark(ctx, rec, 3);
-  count_launches(ctx, 7);
+  count_launches(ctx, 6);
   return launched(ctx, "pd_sgm_band");
 }
 

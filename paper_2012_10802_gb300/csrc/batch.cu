@@ -56,8 +56,7 @@ __global__ void __launch_bounds__(kCostThreads) k_cost_b(const BatchPair* __rest
   const int i = find_pair(starts, npairs, blockIdx.x);
   const BatchPair& p = pairs[i];
   const int b = blockIdx.x - starts[i];
-  const int P = kCostThreads / (p.D >> 4);
-  const int nbx = (p.W + P - 1) / P;
+  const int nbx = cost_blocks_per_row(p.W, p.D);
   cost_il_block(p.cl, p.cr, p.W, p.D, p.cost, b % nbx, b / nbx);
 }
 
@@ -133,8 +132,7 @@ __global__ void k_lr_b(const BatchPair* __restrict__ pairs, const int* __restric
 void batch_stage_blocks(int W, int H, int D, int counts[kBatchStages]) {
   counts[kStageKappa] = (H + 3) / 4;
   counts[kStageCensus] = ((W + kCT_W - 1) / kCT_W) * ((H + kCT_H - 1) / kCT_H);
-  const int Pc = kCostThreads / (D / 16);
-  counts[kStageCost] = ((W + Pc - 1) / Pc) * H;
+  counts[kStageCost] = cost_blocks_per_row(W, D) * H;
   const size_t N = (size_t)W * H;
   counts[kStageFill] = (int)((N + 4095) / 4096);
   const int Pw = kWtaThreads / (D / 16);

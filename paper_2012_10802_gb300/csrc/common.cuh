@@ -95,6 +95,9 @@ void launch_warp(cudaStream_t s, const uint8_t* right, int W, int H, size_t pitc
 // Census of img, or of the row-shifted image when kappa != nullptr.
 void launch_census(cudaStream_t s, const uint8_t* img, int W, int H, size_t pitch,
                    const int32_t* kappa, uint32_t* codes);
+// Census codes of both images of a pair in one launch (the right one through kappa).
+void launch_census_pair(cudaStream_t s, const uint8_t* left, const uint8_t* right, int W, int H,
+                        size_t pitch, const int32_t* kappa, uint32_t* cl, uint32_t* cr);
 // layout 0: natural [H][W][D]; layout 1: the interleaved layout of the aggregation kernels
 // (D % 16 == 0): within each 16-disparity group g, byte 2j holds d = 16g + j and byte 2j+1 holds
 // d = 16g + 8 + j.

@@ -28,11 +28,12 @@ __device__ float slic_gradient(const float* __restrict__ D2, int W, int H, int x
 }
 
 // Sums (count, x, y, q) over the lanes that share a label, one representative lane per label
-// adding them into shared slots (slot >= 0) or straight into the global sums (slot < 0).  All 32
-// lanes must call it; lanes with valid == false contribute nothing.  q is summed exactly in two
-// 16-bit halves.
+// adding them into the tile's 32-bit shared slots (slot >= 0) or straight into the 64-bit global
+// sums (slot < 0).  All 32 lanes must call it; lanes with valid == false contribute nothing.  q
+// is summed in a 16-bit low part and a signed high part; the per-tile sums (at most 1024 pixels)
+// are exact while |q| < 2^37, i.e. |D2| < 2^27 px.
 __device__ void warp_accumulate(bool valid, int lab, int slot, int x, int y, long long q,
-                                unsigned long long (*sacc)[4], unsigned long long* acc) {
+                                unsigned (*sacc)[5], unsigned long long* acc) {
   const int lane = threadIdx.x & 31;
   unsigned pending = __ballot_sync(0xffffffffu, valid);
   while (pending) {
@@ -45,12 +46,21 @@ __device__ void warp_accumulate(bool valid, int lab, int slot, int x, int y, lon
     const unsigned qlo = __reduce_add_sync(0xffffffffu, mine ? (unsigned)(q & 0xffff) : 0u);
     const int qhi = __reduce_add_sync(0xffffffffu, mine ? (int)(q >> 16) : 0);
     if (lane == leader) {
-      const long long qs = (long long)qhi * 65536LL + (long long)qlo;
-      unsigned long long* a = slot >= 0 ? sacc[slot] : acc + 4 * (size_t)lab;
-      atomicAdd(a + 0, (unsigned long long)__popc(peers));
-      atomicAdd(a + 1, (unsigned long long)xs);
-      atomicAdd(a + 2, (unsigned long long)ys);
-      atomicAdd(a + 3, (unsigned long long)qs);
+      if (slot >= 0) {  // per-tile 32-bit sums (exact for |q| < 2^37)
+        unsigned* a = sacc[slot];
+        atomicAdd(a + 0, (unsigned)__popc(peers));
+        atomicAdd(a + 1, (unsigned)xs);
+        atomicAdd(a + 2, (unsigned)ys);
+        atomicAdd(a + 3, qlo);
+        atomicAdd(a + 4, (unsigned)qhi);
+      } else {
+        const long long qs = (long long)qhi * 65536LL + (long long)qlo;
+        unsigned long long* a = acc + 4 * (size_t)lab;
+        atomicAdd(a + 0, (unsigned long long)__popc(peers));
+        atomicAdd(a + 1, (unsigned long long)xs);
+        atomicAdd(a + 2, (unsigned long long)ys);
+        atomicAdd(a + 3, (unsigned long long)qs);
+      }
     }
     pending &= ~peers;
   }
@@ -99,7 +109,7 @@ __global__ void __launch_bounds__(kTileThreads) k_slic_assign(
     int do_assign, int32_t* __restrict__ labels, unsigned long long* __restrict__ acc) {
   __shared__ int cand[kCandCap];
   __shared__ float ccx[kCandCap], ccy[kCandCap], ccv[kCandCap];
-  __shared__ unsigned long long sacc[kCandCap][4];
+  __shared__ unsigned sacc[kCandCap][5];
   __shared__ int wcount[kTileThreads / 32];
   __shared__ int ncand;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -172,7 +182,7 @@ __global__ void __launch_bounds__(kTileThreads) k_slic_assign(
   const int nc = ncand;
   const bool overflow = nc > kCandCap;
   for (int i = tid; i < kCandCap; i += kTileThreads)
-    sacc[i][0] = sacc[i][1] = sacc[i][2] = sacc[i][3] = 0ULL;
+    sacc[i][0] = sacc[i][1] = sacc[i][2] = sacc[i][3] = sacc[i][4] = 0u;
   __syncthreads();
 
 #pragma unroll
@@ -226,12 +236,13 @@ __global__ void __launch_bounds__(kTileThreads) k_slic_assign(
   __syncthreads();
   if (!overflow)
     for (int i = tid; i < nc; i += kTileThreads) {
-      if (sacc[i][0] == 0ULL) continue;
+      if (sacc[i][0] == 0u) continue;
       unsigned long long* a = acc + 4 * (size_t)cand[i];
-      atomicAdd(a + 0, sacc[i][0]);
-      atomicAdd(a + 1, sacc[i][1]);
-      atomicAdd(a + 2, sacc[i][2]);
-      atomicAdd(a + 3, sacc[i][3]);
+      const long long qs = (long long)(int)sacc[i][4] * 65536LL + (long long)sacc[i][3];
+      atomicAdd(a + 0, (unsigned long long)sacc[i][0]);
+      atomicAdd(a + 1, (unsigned long long)sacc[i][1]);
+      atomicAdd(a + 2, (unsigned long long)sacc[i][2]);
+      atomicAdd(a + 3, (unsigned long long)qs);
     }
 
 }

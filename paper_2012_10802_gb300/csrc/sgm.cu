@@ -53,6 +53,17 @@ __global__ void k_census(const uint8_t* __restrict__ img, int W, int H, size_t p
   census_tile(img, W, H, pitch, kappa, codes, blockIdx.x, blockIdx.y);
 }
 
+// Both images of a pair in one launch: blockIdx.z = 0 is the left image, 1 the right image read
+// through the row shifts kappa.
+__global__ void k_census_pair(const uint8_t* __restrict__ left, const uint8_t* __restrict__ right,
+                              int W, int H, size_t pitch, const int32_t* __restrict__ kappa,
+                              uint32_t* __restrict__ cl, uint32_t* __restrict__ cr) {
+  if (blockIdx.z == 0)
+    census_tile(left, W, H, pitch, nullptr, cl, blockIdx.x, blockIdx.y);
+  else
+    census_tile(right, W, H, pitch, kappa, cr, blockIdx.x, blockIdx.y);
+}
+
 __global__ void __launch_bounds__(kCostThreads) k_cost_il(const uint32_t* __restrict__ cl,
                                                           const uint32_t* __restrict__ cr, int W,
                                                           int D, uint8_t* __restrict__ cost) {
@@ -216,11 +227,16 @@ void launch_census(cudaStream_t s, const uint8_t* img, int W, int H, size_t pitc
   k_census<<<grid, dim3(kCT_W, kCT_H), 0, s>>>(img, W, H, pitch, kappa, codes);
 }
 
+void launch_census_pair(cudaStream_t s, const uint8_t* left, const uint8_t* right, int W, int H,
+                        size_t pitch, const int32_t* kappa, uint32_t* cl, uint32_t* cr) {
+  dim3 grid((W + kCT_W - 1) / kCT_W, (H + kCT_H - 1) / kCT_H, 2);
+  k_census_pair<<<grid, dim3(kCT_W, kCT_H), 0, s>>>(left, right, W, H, pitch, kappa, cl, cr);
+}
+
 void launch_cost(cudaStream_t s, const uint32_t* cl, const uint32_t* cr, int W, int H, int D,
                  int layout, uint8_t* cost) {
   if (layout == 1) {
-    int P = kCostThreads / (D / 16);
-    dim3 grid((W + P - 1) / P, H);
+    dim3 grid(cost_blocks_per_row(W, D), H);
     k_cost_il<<<grid, kCostThreads, 0, s>>>(cl, cr, W, D, cost);
   } else {
     size_t per_row = (size_t)W * D;

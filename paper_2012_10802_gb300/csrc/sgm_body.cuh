@@ -89,42 +89,92 @@ __device__ __forceinline__ void census_tile(const uint8_t* __restrict__ img, int
 }
 
 // ----------------------------------------------------------------------------- cost
-// Interleaved layout, D % 16 == 0: one thread per (pixel, 16-disparity group), 16 bytes out.
+// Interleaved layout, D % 16 == 0.  A block covers one segment of kCostSeg(D) pixels of a row
+// from one shared copy of the right codes it needs.  A warp computes one 16-disparity group for
+// 32 consecutive pixels (lane = pixel), so its shared reads are consecutive words at a constant
+// offset per disparity; the 16-byte results go through a swizzled shared tile and leave as
+// contiguous rows of the volume.
 constexpr int kCostThreads = 256;
+constexpr int kCostWarps = kCostThreads / 32;
+constexpr int kCostSlices = 8;
+constexpr int kCostStage = 8192;  // bytes of one pass: max(32, 256 / (D/16)) pixels x D bytes
 
-// Interleaved cost of P = kCostThreads / (D/16) pixels of row v starting at u0 = bx * P.
-__device__ __forceinline__ void cost_il_block(const uint32_t* __restrict__ cl,
-                                              const uint32_t* __restrict__ cr, int W, int D,
-                                              uint8_t* __restrict__ cost, int bx, int v) {
-  __shared__ uint32_t sR[kCostThreads + kMaxD];
-  const int groups = D >> 4;
-  const int P = kCostThreads / groups;  // pixels per block
-  const int u0 = bx * P;
-  const int base = u0 - D + 1;
-  for (int i = threadIdx.x; i < P + D - 1; i += kCostThreads) {
-    int x = base + i;
-    sR[i] = (x >= 0 && x < W) ? cr[(size_t)v * W + x] : 0u;
-  }
-  __syncthreads();
-  const int u = u0 + threadIdx.x / groups;
-  const int g = threadIdx.x % groups;
-  if (u >= W) return;
-  const uint32_t c0 = cl[(size_t)v * W + u];
+__host__ __device__ __forceinline__ int cost_seg(int D) {
+  return kCostSlices * (kCostThreads / (D >> 4));
+}
+__host__ __device__ __forceinline__ int cost_blocks_per_row(int W, int D) {
+  return (W + cost_seg(D) - 1) / cost_seg(D);
+}
+
+__device__ __forceinline__ uint32_t lds32(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+  return v;
+}
+
+// 16 costs of group g for pixel u (codes c0; the right code of d = 16g + dd at shared address
+// r - 4 dd): byte 2j holds d = 16g + j and byte 2j + 1 holds d = 16g + 8 + j.  CHECK: x = u - d
+// may be negative.
+template <bool CHECK>
+__device__ __forceinline__ uint4 cost16(uint32_t c0, uint32_t r, int x0) {
   uint32_t w[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     uint32_t packed = 0;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-      int p = 4 * i + b;
-      int d = 16 * g + (p >> 1) + ((p & 1) << 3);
-      int x = u - d;
-      uint32_t c = x >= 0 ? (uint32_t)__popc(c0 ^ sR[x - base]) : (uint32_t)kCensusBits;
+      const int p = 4 * i + b;
+      const int dd = (p >> 1) + ((p & 1) << 3);  // d - 16g
+      uint32_t c = (uint32_t)__popc(c0 ^ lds32(r - 4u * (uint32_t)dd));
+      if (CHECK && x0 - dd < 0) c = (uint32_t)kCensusBits;
       packed |= c << (8 * b);
     }
     w[i] = packed;
   }
-  *reinterpret_cast<uint4*>(cost + ((size_t)v * W + u) * D + 16 * g) = make_uint4(w[0], w[1], w[2], w[3]);
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Interleaved cost of the segment bx of row v.
+__device__ __forceinline__ void cost_il_block(const uint32_t* __restrict__ cl,
+                                              const uint32_t* __restrict__ cr, int W, int D,
+                                              uint8_t* __restrict__ cost, int bx, int v) {
+  __shared__ uint32_t sR[kCostSlices * kCostThreads + kMaxD];
+  __shared__ __align__(16) uint4 stage[kCostStage / 16];
+  const int groups = D >> 4;
+  const int seg = cost_seg(D);
+  const int u0 = bx * seg;
+  const int base = u0 - D + 1;  // x of sR[0]
+  for (int i = threadIdx.x; i < seg + D - 1; i += kCostThreads) {
+    const int x = base + i;
+    sR[i] = (x >= 0 && x < W) ? cr[(size_t)v * W + x] : 0u;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int pix = kCostStage / D;     // pixels per pass (32 chunk rows of 16 B per group)
+  const int chunks = pix / 32;        // 32-pixel chunks per pass
+  const int gmask = groups - 1;
+  for (int p0 = u0; p0 < u0 + seg && p0 < W; p0 += pix) {
+    __syncthreads();  // sR filled / the previous pass copied out
+    for (int it = warp; it < chunks * groups; it += kCostWarps) {
+      const int g = it % groups, ch = it / groups;
+      const int r = ch * 32 + lane;  // pixel row within the pass
+      const int u = p0 + r;
+      const uint32_t c0 = u < W ? cl[(size_t)v * W + u] : 0u;
+      const uint32_t rp =
+          (uint32_t)__cvta_generic_to_shared(sR) + 4u * (uint32_t)((u - base) - 16 * g);
+      const int x0 = u - 16 * g;  // x of d = 16g
+      const bool check = p0 + ch * 32 - 16 * g - 15 < 0;  // warp-uniform
+      const uint4 val = check ? cost16<true>(c0, rp, x0) : cost16<false>(c0, rp, x0);
+      stage[r * groups + (g ^ (r & gmask))] = val;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < pix * groups; i += kCostThreads) {
+      const int r = i / groups, g = i % groups;
+      const int u = p0 + r;
+      if (u < W)
+        *reinterpret_cast<uint4*>(cost + ((size_t)v * W + u) * D + 16 * g) =
+            stage[r * groups + (g ^ (r & gmask))];
+    }
+  }
 }
 
 // ----------------------------------------------------------------------------- Eq. (8)
