@@ -97,7 +97,8 @@ __global__ void k_slic_init_labels(int W, int H, int nx, int ny, int32_t* __rest
   int x = blockIdx.x * blockDim.x + threadIdx.x;
   int y = blockIdx.y;
   if (x >= W) return;
-  labels[(size_t)y * W + x] = (int32_t)(((long long)y * ny / H) * nx + ((long long)x * nx / W));
+  // y * ny and x * nx stay below 2^28 (W, H <= 16384): 32-bit divisions give the same floors
+  labels[(size_t)y * W + x] = (int32_t)((y * ny / H) * nx + (x * nx / W));
 }
 
 // One assignment round (if do_assign) plus the per-centre sums of the resulting labels:

@@ -150,12 +150,13 @@ __device__ __forceinline__ void cost_il_block(const uint32_t* __restrict__ cl,
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int pix = kCostStage / D;     // pixels per pass (32 chunk rows of 16 B per group)
-  const int chunks = pix / 32;        // 32-pixel chunks per pass
+  const int chunks = pix >> 5;        // 32-pixel chunks per pass
   const int gmask = groups - 1;
+  const int lg = 31 - __clz(groups);  // groups is a power of two: shifts, not divisions
   for (int p0 = u0; p0 < u0 + seg && p0 < W; p0 += pix) {
     __syncthreads();  // sR filled / the previous pass copied out
     for (int it = warp; it < chunks * groups; it += kCostWarps) {
-      const int g = it % groups, ch = it / groups;
+      const int g = it & gmask, ch = it >> lg;
       const int r = ch * 32 + lane;  // pixel row within the pass
       const int u = p0 + r;
       const uint32_t c0 = u < W ? cl[(size_t)v * W + u] : 0u;
@@ -168,7 +169,7 @@ __device__ __forceinline__ void cost_il_block(const uint32_t* __restrict__ cl,
     }
     __syncthreads();
     for (int i = threadIdx.x; i < pix * groups; i += kCostThreads) {
-      const int r = i / groups, g = i % groups;
+      const int r = i >> lg, g = i & gmask;
       const int u = p0 + r;
       if (u < W)
         *reinterpret_cast<uint4*>(cost + ((size_t)v * W + u) * D + 16 * g) =
