@@ -241,11 +241,28 @@ constexpr int kRoundBlocks = 152;
 constexpr int kRoundPoints = kRoundBlocks * kRollWarp;  // shrinks the bracket ~2400x per round
 constexpr int kRefineRounds = 2;                        // 0.02 degree -> below 1e-10 rad
 
+// (energy, index) candidates are compared through an order-preserving int64 key of the energy:
+// FP64 compares cost about 63 cycles each on this GPU, integer compares a few.
 struct RollBest {
-  double e;
+  long long key;
   int k;
   int pad;
 };
+
+// cos, sin and the Eq. (11) coefficients at a refinement block's best angle: the final stage
+// takes the winner's instead of evaluating the angle again (a double sincos and fit cost ~20k
+// cycles of the FP64 pipe).
+struct RollFit {
+  double c, s, beta[3];
+};
+
+// Key whose signed order is the order of the doubles (no NaN occurs: a failed fit is +inf);
+// -0 is folded to +0, so equal energies still tie and the smaller index wins.
+__device__ __forceinline__ long long energy_key(double e) {
+  long long b = __double_as_longlong(e);
+  if (b == (long long)0x8000000000000000ULL) b = 0;
+  return b < 0 ? (b ^ 0x7fffffffffffffffLL) : b;
+}
 
 // Converts the 22 sums (after the count) to doubles, one per lane of the calling warp; the caller
 // synchronises before reading M.
@@ -280,14 +297,14 @@ __device__ double coord_scale_d(int W, int H) {
   return sc;
 }
 
-__device__ __forceinline__ bool better(double e, int k, double eo, int ko) {
+__device__ __forceinline__ bool better(long long e, int k, long long eo, int ko) {
   return eo < e || (eo == e && ko < k);
 }
 
-// Warp-wide (e, k) minimum, smallest k on ties; every lane gets the result.
-__device__ void warp_argmin(double& e, int& k) {
+// Warp-wide (key, k) minimum, smallest k on ties; every lane gets the result.
+__device__ void warp_argmin(long long& e, int& k) {
   for (int o = 16; o > 0; o >>= 1) {
-    double eo = __shfl_xor_sync(0xffffffffu, e, o);
+    long long eo = __shfl_xor_sync(0xffffffffu, e, o);
     int ko = __shfl_xor_sync(0xffffffffu, k, o);
     if (better(e, k, eo, ko)) {
       e = eo;
@@ -297,12 +314,12 @@ __device__ void warp_argmin(double& e, int& k) {
 }
 
 // Minimum over n per-block results, by one warp.
-__device__ void reduce_best(const RollBest* __restrict__ res, int n, double& e, int& k) {
-  e = INFINITY;
+__device__ void reduce_best(const RollBest* __restrict__ res, int n, long long& e, int& k) {
+  e = 0x7fffffffffffffffLL;
   k = 0x7fffffff;
   for (int i = threadIdx.x & 31; i < n; i += 32)
-    if (better(e, k, res[i].e, res[i].k)) {
-      e = res[i].e;
+    if (better(e, k, res[i].key, res[i].k)) {
+      e = res[i].key;
       k = res[i].k;
     }
   warp_argmin(e, k);
@@ -312,8 +329,8 @@ __device__ void reduce_best(const RollBest* __restrict__ res, int n, double& e, 
 // and winning angle after the last round: the best grid angle's neighbours, then for each round
 // the neighbours of its best interior point.
 __device__ void bracket_chain(const RollBest* __restrict__ res, int round, double& a, double& b,
-                              double& phi) {
-  double e;
+                              double& phi, int* last_w = nullptr) {
+  long long e;
   int w;
   reduce_best(res, kGridBlocks, e, w);
   int best = w < kGridN ? w : 0;
@@ -331,6 +348,7 @@ __device__ void bracket_chain(const RollBest* __restrict__ res, int round, doubl
     const double nb = a + h * (double)(w + 2);
     a = na;
     b = nb;
+    if (last_w) *last_w = w;
   }
 }
 
@@ -350,14 +368,16 @@ __global__ void __launch_bounds__(kRollWarp) k_roll_grid(const int64_t* __restri
     e = e0min_cs(M, order, coord_scale_d(W, H), cp, sp, beta);
   }
   int kk = k < kGridN ? k : 0x7fffffff;
-  warp_argmin(e, kk);
-  if (threadIdx.x == 0) res[blockIdx.x] = RollBest{e, kk, 0};
+  long long key = energy_key(e);
+  warp_argmin(key, kk);
+  if (threadIdx.x == 0) res[blockIdx.x] = RollBest{key, kk, 0};
 }
 
 // Refinement round: kRoundPoints interior points of the current bracket.
 __global__ void __launch_bounds__(kRollWarp) k_roll_round(const int64_t* __restrict__ sums,
                                                           int order, int W, int H, int round,
-                                                          RollBest* __restrict__ res) {
+                                                          RollBest* __restrict__ res,
+                                                          RollFit* __restrict__ fits) {
   __shared__ MomD M;
   load_moments(sums, M);
   __syncthreads();
@@ -374,10 +394,14 @@ __global__ void __launch_bounds__(kRollWarp) k_roll_round(const int64_t* __restr
   const double ct = 1.0 - t2 * (0.5 - t2 * (1.0 / 24.0 - t2 * (1.0 / 720.0)));
   const double st = t * (1.0 - t2 * (1.0 / 6.0 - t2 * (1.0 / 120.0 - t2 * (1.0 / 5040.0))));
   double beta[3];
-  double e = e0min_cs(M, order, coord_scale_d(W, H), ca * ct - sa * st, sa * ct + ca * st, beta);
+  const double cphi = ca * ct - sa * st, sphi = sa * ct + ca * st;
+  double e = e0min_cs(M, order, coord_scale_d(W, H), cphi, sphi, beta);
   int k = i;
-  warp_argmin(e, k);
-  if (threadIdx.x == 0) res[kGridBlocks + (round - 1) * kRoundBlocks + blockIdx.x] = RollBest{e, k, 0};
+  long long key = energy_key(e);
+  warp_argmin(key, k);
+  if (threadIdx.x == 0)
+    res[kGridBlocks + (round - 1) * kRoundBlocks + blockIdx.x] = RollBest{key, k, 0};
+  if (i == k) fits[(round - 1) * kRoundBlocks + blockIdx.x] = RollFit{cphi, sphi, {beta[0], beta[1], beta[2]}};
 }
 
 // Final stage (one warp): the roll (order 2: the winner of the last round; order 1: the
@@ -385,6 +409,7 @@ __global__ void __launch_bounds__(kRollWarp) k_roll_round(const int64_t* __restr
 // form for the transform kernel.
 __global__ void __launch_bounds__(kRollWarp) k_roll_final(const int64_t* __restrict__ sums,
                                                           const RollBest* __restrict__ res,
+                                                          const RollFit* __restrict__ fits,
                                                           int order, int W, int H,
                                                           pd_road_model* fitted,
                                                           RoadCoefF* coef) {
@@ -393,9 +418,10 @@ __global__ void __launch_bounds__(kRollWarp) k_roll_final(const int64_t* __restr
   __syncthreads();
   const double sc = coord_scale_d(W, H);
   double phi = 0.0;
+  int w = 0;
   if (order == 2) {
     double a, b;
-    bracket_chain(res, kRefineRounds + 1, a, b, phi);
+    bracket_chain(res, kRefineRounds + 1, a, b, phi, &w);
   }
   if (threadIdx.x != 0) return;
   if (order == 1) {
@@ -408,8 +434,15 @@ __global__ void __launch_bounds__(kRollWarp) k_roll_final(const int64_t* __restr
     if (spd_solve_d(3, A, b, x) == 0 && x[1] != 0.0) phi = atan(-x[2] / x[1]);
   }
   double beta[3];
-  {
-    double sp, cp;
+  double sp, cp;
+  if (order == 2) {  // the last round evaluated this angle already: its block kept the fit
+    const RollFit f = fits[(kRefineRounds - 1) * kRoundBlocks + w / kRollWarp];
+    cp = f.c;
+    sp = f.s;
+    beta[0] = f.beta[0];
+    beta[1] = f.beta[1];
+    beta[2] = f.beta[2];
+  } else {
     sincos(phi, &sp, &cp);
     e0min_cs(M, order, sc, cp, sp, beta);
   }
@@ -432,8 +465,8 @@ __global__ void __launch_bounds__(kRollWarp) k_roll_final(const int64_t* __restr
     w[4] = (unsigned long long)__double_as_longlong(out.roll);
   }
   RoadCoefF cf;
-  cf.c = (float)cos(phi);
-  cf.s = (float)sin(phi);
+  cf.c = (float)cp;
+  cf.s = (float)sp;
   cf.a0 = (float)out.a[0];
   cf.a1 = (float)out.a[1];
   cf.a2 = order == 2 ? (float)out.a[2] : 0.0f;
@@ -468,8 +501,11 @@ size_t moments_scratch_bytes(int W, int H) {
   return n * kNumSums * sizeof(long long);
 }
 
+constexpr size_t kRollFitsOffset = (size_t)(kGridBlocks + kRefineRounds * kRoundBlocks) * sizeof(RollBest);
+static_assert(kRollFitsOffset % alignof(RollFit) == 0, "RollFit alignment");
+
 size_t roll_scratch_bytes() {
-  return (size_t)(kGridBlocks + kRefineRounds * kRoundBlocks) * sizeof(RollBest);
+  return kRollFitsOffset + (size_t)kRefineRounds * kRoundBlocks * sizeof(RollFit);
 }
 
 void launch_moments(cudaStream_t s, const float* D1, int W, int H, void* scratch, int64_t* sums,
@@ -483,14 +519,15 @@ void launch_moments(cudaStream_t s, const float* D1, int W, int H, void* scratch
 int launch_roll_solve(cudaStream_t s, const int64_t* sums, int order, int W, int H,
                       pd_road_model* fitted, RoadCoefF* coef, double* grid_scratch) {
   RollBest* res = reinterpret_cast<RollBest*>(grid_scratch);
+  RollFit* fits = reinterpret_cast<RollFit*>(reinterpret_cast<char*>(grid_scratch) + kRollFitsOffset);
   int n = 1;
   if (order == 2) {
     k_roll_grid<<<kGridBlocks, kRollWarp, 0, s>>>(sums, order, W, H, res);
     for (int r = 1; r <= kRefineRounds; ++r)
-      k_roll_round<<<kRoundBlocks, kRollWarp, 0, s>>>(sums, order, W, H, r, res);
+      k_roll_round<<<kRoundBlocks, kRollWarp, 0, s>>>(sums, order, W, H, r, res, fits);
     n += 1 + kRefineRounds;
   }
-  k_roll_final<<<1, kRollWarp, 0, s>>>(sums, res, order, W, H, fitted, coef);
+  k_roll_final<<<1, kRollWarp, 0, s>>>(sums, res, fits, order, W, H, fitted, coef);
   return n;
 }
 
