@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-pair mixed batch")
     ap.add_argument("--no-band", action="store_true", help="skip the learned-band comparison")
     ap.add_argument("--no-stream", action="store_true", help="skip the closed-loop drive")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="enqueue every kernel directly instead of replaying the captured path")
     ap.add_argument("--band-size", default=None,
                     help="WxH: only time pd_sgm_band on a road of that size with every tile "
                          "banded around its full-range median (for profiling)")
@@ -447,6 +449,7 @@ def main():
     model = B.RoadModel.make(*synth.true_model(sc))
     params = B.default_params()
     ctx = B.Context(local)
+    B.pd_pipeline_config(ctx, not args.no_graph)  # replay the captured path (CUDA graph)
     left = torch.from_numpy(left_np).cuda()
     right = torch.from_numpy(right_np).cuda()
     outs = B.make_outputs(ctx, W_, H_)
@@ -573,6 +576,7 @@ def main():
         "dtype": "u16+f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "W": W_, "H": H_, "D": D_, "paths": PATHS_,
                    "l2": "flushed before each timed step (256 MiB write)",
+                   "cuda_graph": not args.no_graph,
                    "frames_per_s": args.steps * world / (t_max * 1e-3),
                    "sgm_only_ms": sgm_ms, "sgm_only_Mdisp_s": W_ * H_ * D_ / (sgm_ms * 1e-3) / 1e6,
                    "stage_ms": {k: prof[k] / calls for k in ("prep_ms", "aggregate_ms",

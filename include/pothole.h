@@ -448,6 +448,17 @@ pd_status pd_run_pipeline_dev(pd_ctx* ctx, const uint8_t* left, const uint8_t* r
                               const pd_params* params, const pd_outputs* out,
                               pd_stage_times* times);
 
+/* CUDA-graph replay of the whole path (pd_run_pipeline and pd_run_pipeline_dev).
+ *  - use_graph != 0: a call without stage times (times == NULL) captures its enqueued sequence
+ *    once into a CUDA graph (on a private capture stream) and replays it on the context's stream
+ *    while the inputs, outputs, parameters, road model (its value for pd_run_pipeline, its
+ *    address for pd_run_pipeline_dev), scratch and profiling state are those of the capture;
+ *    any change captures again.  Results are identical to direct enqueueing.  Profiled calls keep
+ *    their per-stage times: the graph's stage marks are retargeted to each call's events.
+ *  - use_graph == 0 (default): every call enqueues its kernels directly; a held graph is freed.
+ * Returns PD_OK, or PD_ERR_INVALID_ARG for a NULL context. */
+pd_status pd_pipeline_config(pd_ctx* ctx, int use_graph);
+
 #ifdef __cplusplus
 }
 #endif

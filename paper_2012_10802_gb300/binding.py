@@ -123,6 +123,7 @@ SIGNATURES = {
     "pd_batch_config": [_P, C.c_size_t, _i, _i],
     "pd_sgm_batch": [_P, C.POINTER(Pair), _i, C.POINTER(Params)],
     "pd_profile_enable": [_P, _i],
+    "pd_pipeline_config": [_P, _i],
     "pd_profile_read": [_P, C.POINTER(Profile)],
 }
 EXTRA = {"pd_last_error": (C.c_char_p, [_P]), "pd_workspace_bytes": (C.c_size_t, [_P]),
@@ -571,6 +572,12 @@ def road_model_tensor(ctx, model):
 
 def pd_profile_enable(ctx, on=True):
     ctx.check(lib().pd_profile_enable(ctx.h, 1 if on else 0))
+
+
+def pd_pipeline_config(ctx, use_graph=True):
+    """Replays pd_run_pipeline / pd_run_pipeline_dev from a captured CUDA graph while the call is
+    the captured one (see include/pothole.h)."""
+    ctx.check(lib().pd_pipeline_config(ctx.h, 1 if use_graph else 0))
 
 
 def pd_profile_read(ctx):

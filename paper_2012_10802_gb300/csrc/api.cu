@@ -101,6 +101,11 @@ pd_prof_rec* prof_begin(pd_ctx* c) {
 
 void mark(pd_ctx* c, pd_prof_rec* r, int i) {
   if (!r) return;
+  if (r == &c->cap_rec) {  // capturing: an external event-record node, retargeted per replay
+    cudaEventRecordWithFlags(c->cap_ev[i], c->stream, cudaEventRecordExternal);
+    c->cap_used |= 1 << i;
+    return;
+  }
   if (!r->ev[i] && cudaEventCreate(&r->ev[i]) != cudaSuccess) {
     cudaGetLastError();
     r->ev[i] = nullptr;
@@ -110,8 +115,8 @@ void mark(pd_ctx* c, pd_prof_rec* r, int i) {
   r->used |= 1 << i;
 }
 
-void count_launches(pd_ctx* c, int n) {
-  if (c->prof) c->launches += n;
+void count_launches(pd_ctx* c, long long n) {
+  if (c->prof && !c->capturing) c->launches += n;
 }
 bool pow2_d(int D) { return D == 32 || D == 64 || D == 128 || D == 256; }
 
@@ -552,6 +557,10 @@ extern "C" pd_status pd_sgm_batch(pd_ctx* ctx, const pd_pair* pairs, int n, cons
 
 extern "C" {
 
+namespace {
+void pipe_graph_free(pd_ctx* ctx);
+}  // namespace
+
 pd_status pd_create(pd_ctx** out, int device, void* stream) {
   if (!out) return PD_ERR_INVALID_ARG;
   *out = nullptr;
@@ -587,6 +596,10 @@ pd_status pd_destroy(pd_ctx* ctx) {
   }
   if (ctx->batch_done) cudaEventDestroy(ctx->batch_done);
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  pipe_graph_free(ctx);
+  for (auto& e : ctx->cap_ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   delete static_cast<std::vector<long long>*>(ctx->graph_sig);
   delete static_cast<std::map<std::vector<long long>, int>*>(ctx->tuned);
@@ -902,8 +915,25 @@ namespace {
 pd_status pipeline_impl(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H,
                         size_t pitch, const pd_road_model* model, const pd_road_model* model_dev,
                         const pd_params* p, const pd_outputs* out, pd_stage_times* times);
+pd_status pipeline_enqueue(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H,
+                           size_t pitch, const pd_road_model* model,
+                           const pd_road_model* model_dev, const pd_params* p,
+                           const pd_outputs* out, bool ccl, int conn, int max_comps,
+                           pd_prof_rec* rec, pd_stage_times* times);
+pd_status pipeline_graph_run(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H,
+                             size_t pitch, const pd_road_model* model,
+                             const pd_road_model* model_dev, const pd_params* p,
+                             const pd_outputs* out, bool ccl, int conn, int max_comps);
+void pipe_graph_free(pd_ctx* ctx);
 
 }  // namespace
+
+pd_status pd_pipeline_config(pd_ctx* ctx, int use_graph) {
+  PD_TRY(begin(ctx));
+  ctx->pipe_graph = use_graph != 0;
+  if (!ctx->pipe_graph) pipe_graph_free(ctx);
+  return PD_OK;
+}
 
 pd_status pd_run_pipeline(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H,
                           size_t pitch, const pd_road_model* model, const pd_params* p,
@@ -941,6 +971,8 @@ pd_status pipeline_impl(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, 
   PD_REQUIRE(p->slic_iters >= 0 && p->slic_iters <= 1000, "slic_iters out of range");
   PD_REQUIRE(p->threshold_mode == 0 || p->threshold_mode == 1, "threshold_mode must be 0 or 1");
   PD_REQUIRE(isfinite(p->delta_dt) && isfinite(p->delta_pd), "non-finite delta");
+  PD_REQUIRE(p->fit_iters >= 0 && p->fit_iters <= 16 && isfinite(p->fit_tau) && p->fit_tau > 0.0f,
+             "fit_iters must be in 0..16 and fit_tau positive");
   const bool ccl = out->components != nullptr;
   const int conn = out->connectivity == 0 ? 8 : out->connectivity;
   if (ccl) {
@@ -959,16 +991,36 @@ pd_status pipeline_impl(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, 
   if (ccl && ccl_scratch_bytes(W, H, max_comps) > other) other = ccl_scratch_bytes(W, H, max_comps);
   if (other > need) need = other;
   PD_TRY(ensure_ws(ctx, need));
+  if (ctx->pipe_graph && !times)
+    return pipeline_graph_run(ctx, left, right, W, H, pitch, model, model_dev, p, out, ccl, conn,
+                              max_comps);
   if (times && !ctx->ev[0])
     for (auto& e : ctx->ev) PD_TRY(cuda_ok(ctx, cudaEventCreate(&e), "cudaEventCreate"));
+  PD_TRY(pipeline_enqueue(ctx, left, right, W, H, pitch, model, model_dev, p, out, ccl, conn,
+                          max_comps, prof_begin(ctx), times));
+  if (times) {
+    PD_TRY(cuda_ok(ctx, cudaEventSynchronize(ctx->ev[4]), "pipeline"));
+    cudaEventElapsedTime(&times->sgm_ms, ctx->ev[0], ctx->ev[1]);
+    cudaEventElapsedTime(&times->transform_ms, ctx->ev[1], ctx->ev[2]);
+    cudaEventElapsedTime(&times->superpixel_ms, ctx->ev[2], ctx->ev[3]);
+    cudaEventElapsedTime(&times->mask_ms, ctx->ev[3], ctx->ev[4]);
+    cudaEventElapsedTime(&times->total_ms, ctx->ev[0], ctx->ev[4]);
+  }
+  return PD_OK;
+}
+
+// The whole path's enqueued sequence (arguments validated, scratch sized).  rec: profiling
+// record (or the capture stand-in, or NULL); times: record the stage events of pd_stage_times.
+pd_status pipeline_enqueue(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H,
+                           size_t pitch, const pd_road_model* model,
+                           const pd_road_model* model_dev, const pd_params* p,
+                           const pd_outputs* out, bool ccl, int conn, int max_comps,
+                           pd_prof_rec* rec, pd_stage_times* times) {
   cudaStream_t s = ctx->stream;
-  pd_prof_rec* rec = prof_begin(ctx);
   if (times) cudaEventRecord(ctx->ev[0], s);
   PD_TRY(sgm_enqueue(ctx, left, right, W, H, pitch, model, p, out->kappa, out->d_int, out->D1,
                      rec, model_dev));
   if (times) cudaEventRecord(ctx->ev[1], s);
-  PD_REQUIRE(p->fit_iters >= 0 && p->fit_iters <= 16 && isfinite(p->fit_tau) && p->fit_tau > 0.0f,
-             "fit_iters must be in 0..16 and fit_tau positive");
   PD_TRY(transform_enqueue(ctx, out->D1, W, H, p->model_order, p->delta_dt, out->fitted,
                            out->D2, ctx->ws, p->fit_iters, p->fit_tau));
   mark(ctx, rec, 4);
@@ -985,15 +1037,120 @@ pd_status pipeline_impl(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, 
                                    out->comps, max_comps, out->n_comps, ctx->ws));
   mark(ctx, rec, 6);
   if (times) cudaEventRecord(ctx->ev[4], s);
-  PD_TRY(launched(ctx, "pd_run_pipeline"));
-  if (times) {
-    PD_TRY(cuda_ok(ctx, cudaEventSynchronize(ctx->ev[4]), "pipeline"));
-    cudaEventElapsedTime(&times->sgm_ms, ctx->ev[0], ctx->ev[1]);
-    cudaEventElapsedTime(&times->transform_ms, ctx->ev[1], ctx->ev[2]);
-    cudaEventElapsedTime(&times->superpixel_ms, ctx->ev[2], ctx->ev[3]);
-    cudaEventElapsedTime(&times->mask_ms, ctx->ev[3], ctx->ev[4]);
-    cudaEventElapsedTime(&times->total_ms, ctx->ev[0], ctx->ev[4]);
+  return launched(ctx, "pd_run_pipeline");
+}
+
+void pipe_graph_free(pd_ctx* ctx) {
+  if (ctx->pipe_exec) cudaGraphExecDestroy(ctx->pipe_exec);
+  if (ctx->pipe_src) cudaGraphDestroy(ctx->pipe_src);
+  delete static_cast<std::vector<unsigned char>*>(ctx->pipe_key);
+  ctx->pipe_exec = nullptr;
+  ctx->pipe_src = nullptr;
+  ctx->pipe_key = nullptr;
+  ctx->pipe_kernels = 0;
+  ctx->cap_used = 0;
+}
+
+// Captures the whole path on the capture stream into ctx->pipe_exec.
+pd_status pipeline_capture(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H,
+                           size_t pitch, const pd_road_model* model,
+                           const pd_road_model* model_dev, const pd_params* p,
+                           const pd_outputs* out, bool ccl, int conn, int max_comps,
+                           const std::vector<unsigned char>& key) {
+  pipe_graph_free(ctx);
+  if (!ctx->cap_stream)
+    PD_TRY(cuda_ok(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking),
+                   "cudaStreamCreateWithFlags"));
+  for (auto& e : ctx->cap_ev)
+    if (!e) PD_TRY(cuda_ok(ctx, cudaEventCreate(&e), "cudaEventCreate"));
+  cudaStream_t user = ctx->stream;
+  ctx->stream = ctx->cap_stream;
+  ctx->capturing = true;
+  ctx->cap_used = 0;
+  pd_status st = cuda_ok(ctx, cudaStreamBeginCapture(ctx->cap_stream,
+                                                     cudaStreamCaptureModeThreadLocal),
+                         "cudaStreamBeginCapture");
+  cudaGraph_t g = nullptr;
+  if (st == PD_OK) {
+    st = pipeline_enqueue(ctx, left, right, W, H, pitch, model, model_dev, p, out, ccl, conn,
+                          max_comps, ctx->prof ? &ctx->cap_rec : nullptr, nullptr);
+    const cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);  // always ends the capture
+    if (st == PD_OK) st = cuda_ok(ctx, e, "cudaStreamEndCapture");
   }
+  ctx->capturing = false;
+  ctx->stream = user;
+  if (st == PD_OK) st = cuda_ok(ctx, cudaGraphInstantiate(&ctx->pipe_exec, g, 0), "cudaGraphInstantiate");
+  if (st != PD_OK) {
+    if (g) cudaGraphDestroy(g);
+    ctx->pipe_exec = nullptr;
+    return st;
+  }
+  ctx->pipe_src = g;
+  size_t n = 0;
+  cudaGraphGetNodes(g, nullptr, &n);
+  std::vector<cudaGraphNode_t> nodes(n);
+  cudaGraphGetNodes(g, nodes.data(), &n);
+  for (cudaGraphNode_t node : nodes) {
+    cudaGraphNodeType t;
+    cudaGraphNodeGetType(node, &t);
+    if (t == cudaGraphNodeTypeKernel) ++ctx->pipe_kernels;
+    if (t == cudaGraphNodeTypeEventRecord) {
+      cudaEvent_t ev = nullptr;
+      cudaGraphEventRecordNodeGetEvent(node, &ev);
+      for (int i = 0; i < 7; ++i)
+        if (ev == ctx->cap_ev[i]) ctx->cap_node[i] = node;
+    }
+  }
+  ctx->pipe_key = new std::vector<unsigned char>(key);
+  return cuda_ok(ctx, cudaGetLastError(), "pipeline graph");
+}
+
+// Replays the captured path (capturing it first when the call differs from the captured one).
+pd_status pipeline_graph_run(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H,
+                             size_t pitch, const pd_road_model* model,
+                             const pd_road_model* model_dev, const pd_params* p,
+                             const pd_outputs* out, bool ccl, int conn, int max_comps) {
+  std::vector<unsigned char> key;
+  auto put = [&key](const void* v, size_t bytes) {
+    const unsigned char* b = static_cast<const unsigned char*>(v);
+    key.insert(key.end(), b, b + bytes);
+  };
+  put(&left, sizeof left);
+  put(&right, sizeof right);
+  put(&W, sizeof W);
+  put(&H, sizeof H);
+  put(&pitch, sizeof pitch);
+  if (model)
+    put(model, sizeof *model);
+  else
+    put(&model_dev, sizeof model_dev);
+  put(p, sizeof *p);
+  put(out, sizeof *out);
+  put(&ctx->ws, sizeof ctx->ws);
+  const int prof = ctx->prof ? 1 : 0;
+  put(&prof, sizeof prof);
+  const auto* held = static_cast<const std::vector<unsigned char>*>(ctx->pipe_key);
+  if (!ctx->pipe_exec || !held || *held != key)
+    PD_TRY(pipeline_capture(ctx, left, right, W, H, pitch, model, model_dev, p, out, ccl, conn,
+                            max_comps, key));
+  if (ctx->prof) {
+    // this call's profiling record receives the stage marks; with the record ring full they go
+    // back to the capture events so that no earlier record is overwritten
+    pd_prof_rec* rec = prof_begin(ctx);
+    for (int i = 0; i < 7; ++i) {
+      if (!(ctx->cap_used >> i & 1)) continue;
+      cudaEvent_t ev = ctx->cap_ev[i];
+      if (rec) {
+        if (!rec->ev[i]) PD_TRY(cuda_ok(ctx, cudaEventCreate(&rec->ev[i]), "cudaEventCreate"));
+        ev = rec->ev[i];
+        rec->used |= 1 << i;
+      }
+      PD_TRY(cuda_ok(ctx, cudaGraphExecEventRecordNodeSetEvent(ctx->pipe_exec, ctx->cap_node[i], ev),
+                     "cudaGraphExecEventRecordNodeSetEvent"));
+    }
+  }
+  PD_TRY(cuda_ok(ctx, cudaGraphLaunch(ctx->pipe_exec, ctx->stream), "cudaGraphLaunch"));
+  count_launches(ctx, ctx->pipe_kernels);
   return PD_OK;
 }
 

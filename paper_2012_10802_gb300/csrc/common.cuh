@@ -36,6 +36,18 @@ struct pd_ctx {
   pd_prof_rec* recs = nullptr;  // kMaxProf records, events created on first use
   int nrec = 0;
   long long launches = 0;       // kernels launched by profiled calls
+  // whole-path graph (pd_pipeline_config)
+  bool pipe_graph = false;
+  cudaStream_t cap_stream = nullptr;  // capture stream: the legacy stream cannot be captured
+  cudaGraph_t pipe_src = nullptr;     // captured graph (its nodes address the exec's)
+  cudaGraphExec_t pipe_exec = nullptr;
+  void* pipe_key = nullptr;           // std::vector<unsigned char>* of the captured call
+  long long pipe_kernels = 0;         // kernel nodes of the graph
+  bool capturing = false;
+  pd_prof_rec cap_rec = {};           // stands for the profiling record while capturing
+  cudaEvent_t cap_ev[7] = {};         // events of the captured stage marks
+  cudaGraphNode_t cap_node[7] = {};
+  int cap_used = 0;
 };
 
 namespace pd {

@@ -375,7 +375,7 @@ __device__ long long block_scan_ll(long long v, long long* tmp) {
 
 __global__ void __launch_bounds__(kSolveThreads) k_thresh_solve(
     const unsigned long long* __restrict__ hist, float delta_pd, int mode,
-    double* __restrict__ thr, double* __restrict__ E2) {
+    double* __restrict__ thr, float* __restrict__ thr_up, double* __restrict__ E2) {
   __shared__ long long tmp[kSolveThreads / 32];
   __shared__ double sE[kSolveThreads];
   __shared__ int sK[kSolveThreads];
@@ -437,18 +437,22 @@ __global__ void __launch_bounds__(kSolveThreads) k_thresh_solve(
   if (isnan(sE[0])) {
     thr[0] = NAN;
     thr[1] = -INFINITY;
+    *thr_up = -INFINITY;
     return;
   }
   thr[0] = (double)sK[0] * 0.125;
   thr[1] = (mode == 0 ? sMean[0] : thr[0]) - (double)delta_pd;
+  *thr_up = __double2float_ru(thr[1]);
 }
 
-__global__ void k_mask(const float* __restrict__ D3, size_t N, const double* __restrict__ thr,
+// D3 < t_s (Eq. 17's pothole rule) in float: for a float x and a double t, x < t exactly when
+// x < tf with tf = t rounded up to a float (no float lies strictly between t and tf; infinities
+// and NaN compare the same), which spares a per-pixel conversion on the FP64 pipe.
+__global__ void k_mask(const float* __restrict__ D3, size_t N, const float* __restrict__ thr_up,
                        uint8_t* __restrict__ mask) {
   size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
-  double ts = thr[1];
-  mask[p] = (double)D3[p] < ts ? 1 : 0;
+  mask[p] = D3[p] < *thr_up ? 1 : 0;
 }
 
 }  // namespace
@@ -504,6 +508,7 @@ size_t threshold_scratch_bytes() {
   size_t acc = 0;
   carve_size<unsigned long long>(acc, 2 * kBins * 4);
   carve_size<double>(acc, 2);
+  carve_size<float>(acc, 1);
   return acc;
 }
 
@@ -513,6 +518,7 @@ int launch_threshold(cudaStream_t s, const float* D2, const float* D1, const flo
   Carve c(scratch);
   unsigned long long* hist = c.take<unsigned long long>(2 * kBins * 4);
   double* thr = c.take<double>(2);
+  float* thr_up = c.take<float>(1);
   if (thresholds) thr = thresholds;
   cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * 2 * kBins * 4, s);
   // about 8 resident blocks per SM: each warp's per-bin loop is a latency chain, so the kernel
@@ -521,9 +527,9 @@ int launch_threshold(cudaStream_t s, const float* D2, const float* D1, const flo
   int yb = (8 * 152 + xb - 1) / xb;
   yb = yb < H ? yb : H;
   k_thresh_hist<<<dim3(xb, yb), 256, 0, s>>>(D2, D1, W, H, hist);
-  k_thresh_solve<<<1, kSolveThreads, 0, s>>>(hist, delta_pd, mode, thr, E2);
+  k_thresh_solve<<<1, kSolveThreads, 0, s>>>(hist, delta_pd, mode, thr, thr_up, E2);
   size_t N = (size_t)W * H;
-  k_mask<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(D3, N, thr, mask);
+  k_mask<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(D3, N, thr_up, mask);
   return 3;
 }
 

@@ -250,6 +250,22 @@ def test_pothole_mask_ragged_and_invalid(orc, B, ctx, W, H):
     assert np.array_equal(host(mask), orc.mask(D2, t[1]))
 
 
+def test_pothole_mask_threshold_edges(orc, B, ctx):
+    """D3 values at and next to t_s in float: the GPU's float comparison against t_s rounded up
+    gives the oracle's (double) D3 < t_s for every one of them."""
+    D1, D2 = _D2(orc, 320, 240, 32, 41)
+    rc, t_r, t_s, _ = orc.threshold(D2, D1, 2.36, 0)
+    assert rc == 0
+    f = np.float32(t_s)
+    vals = [f, np.nextafter(f, np.float32(-np.inf)), np.nextafter(f, np.float32(np.inf)),
+            np.float32(t_s - 1e-9), np.float32(t_s + 1e-9), np.float32(-np.inf),
+            np.float32(np.inf), np.float32(np.nan), np.float32(0.0)]
+    D3 = np.resize(np.array(vals, np.float32), D2.shape).astype(np.float32)
+    mask, thr = B.pd_pothole_mask(ctx, dev(D2), dev(D1), dev(D3), 2.36, 0)
+    assert host(thr)[1] == t_s
+    assert np.array_equal(host(mask), orc.mask(D3, t_s))
+
+
 def test_pothole_mask_empty_split(orc, B, ctx):
     """A constant map has no threshold with two non-empty clusters: t_r is NaN, no pothole."""
     D2 = np.full((40, 50), 16.0, np.float32)
