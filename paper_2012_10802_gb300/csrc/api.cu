@@ -1051,13 +1051,14 @@ void pipe_graph_free(pd_ctx* ctx) {
   ctx->cap_used = 0;
 }
 
-// Captures the whole path on the capture stream into ctx->pipe_exec.
+// Captures the whole path on the capture stream into ctx->pipe_exec.  A held executable of the
+// same shape (kernels, copies, marks) is updated in place, which is cheaper than a new
+// instantiation; the graph it was instantiated from keeps addressing its nodes.
 pd_status pipeline_capture(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H,
                            size_t pitch, const pd_road_model* model,
                            const pd_road_model* model_dev, const pd_params* p,
                            const pd_outputs* out, bool ccl, int conn, int max_comps,
                            const std::vector<unsigned char>& key) {
-  pipe_graph_free(ctx);
   if (!ctx->cap_stream)
     PD_TRY(cuda_ok(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking),
                    "cudaStreamCreateWithFlags"));
@@ -1079,9 +1080,26 @@ pd_status pipeline_capture(pd_ctx* ctx, const uint8_t* left, const uint8_t* righ
   }
   ctx->capturing = false;
   ctx->stream = user;
-  if (st == PD_OK) st = cuda_ok(ctx, cudaGraphInstantiate(&ctx->pipe_exec, g, 0), "cudaGraphInstantiate");
   if (st != PD_OK) {
     if (g) cudaGraphDestroy(g);
+    pipe_graph_free(ctx);
+    return st;
+  }
+  const int used = ctx->cap_used;
+  if (ctx->pipe_exec) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(ctx->pipe_exec, g, &info) == cudaSuccess) {
+      cudaGraphDestroy(g);
+      *static_cast<std::vector<unsigned char>*>(ctx->pipe_key) = key;
+      return PD_OK;
+    }
+    cudaGetLastError();  // a different shape: instantiate anew
+  }
+  pipe_graph_free(ctx);
+  ctx->cap_used = used;
+  st = cuda_ok(ctx, cudaGraphInstantiate(&ctx->pipe_exec, g, 0), "cudaGraphInstantiate");
+  if (st != PD_OK) {
+    cudaGraphDestroy(g);
     ctx->pipe_exec = nullptr;
     return st;
   }
