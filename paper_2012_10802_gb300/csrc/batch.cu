@@ -161,7 +161,7 @@ void launch_batch_wave(cudaStream_t s, const BatchWaveDev& w, int P1, int P2, in
   raise_smem_limit((const void*)k_aggregate_b, smem);
   k_aggregate_b<<<agg_blocks, agg_warps * 32, smem, s>>>(w.pairs, w.segs, w.nseg, w.ntasks,
                                                          w.counter, P1x2, K21x2);
-  k_wta_b<<<w.total[kStageWta], kWtaThreads, 4096 * sizeof(uint16_t), s>>>(
+  k_wta_b<<<w.total[kStageWta], kWtaThreads, (size_t)kWtaThreads * 16 * sizeof(uint16_t), s>>>(
       w.pairs, w.starts[kStageWta], n, paths);
   k_lr_b<<<w.total[kStageLr], 256, 0, s>>>(w.pairs, w.starts[kStageLr], n, lr_tol);
 }
