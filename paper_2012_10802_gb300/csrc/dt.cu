@@ -19,6 +19,7 @@ namespace {
 
 constexpr int kMomThreads = 256;
 constexpr int kMomPixPerBlock = 2048;  // keeps every per-block int64 partial exact (W, H <= 4096)
+static_assert(kMomPixPerBlock % kMomThreads == 0, "whole pixels per thread");
 constexpr int kNumSums = 23;
 
 __device__ __forceinline__ long long warp_sum_ll(long long x) {
@@ -51,9 +52,20 @@ __global__ void __launch_bounds__(kMomThreads) k_moments_partial(const float* __
   const size_t N = (size_t)W * H;
   const size_t start = (size_t)blockIdx.x * kMomPixPerBlock;
   const size_t end = min(start + (size_t)kMomPixPerBlock, N);
-  for (size_t p = start + threadIdx.x; p < end; p += kMomThreads) {
-    float d = D1[p];
-    if (!(d >= 0.0f)) continue;
+  // the thread's kMomPixPerBlock / kMomThreads disparities are loaded together first, so their
+  // memory latencies overlap instead of adding up
+  constexpr int kPer = kMomPixPerBlock / kMomThreads;
+  float dv[kPer];
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const size_t p = start + threadIdx.x + (size_t)j * kMomThreads;
+    dv[j] = p < end ? D1[p] : -1.0f;
+  }
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const size_t p = start + threadIdx.x + (size_t)j * kMomThreads;
+    const float d = dv[j];
+    if (!(d >= 0.0f)) continue;  // also every p >= end
     const int pi = (int)p;  // W * H <= 2^24: a 32-bit division
     int u = pi % W, v = pi / W;
     if (fit && !(fabsf(d - road_f32(cf, u, v)) <= tau)) continue;
