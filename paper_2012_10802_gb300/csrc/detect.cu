@@ -186,53 +186,84 @@ __global__ void __launch_bounds__(kTileThreads) k_slic_assign(
     sacc[i][0] = sacc[i][1] = sacc[i][2] = sacc[i][3] = sacc[i][4] = 0u;
   __syncthreads();
 
+  // A thread takes two pixels per pass, rows y and y + kTile / 2 of its column: each candidate's
+  // shared loads and x distance then serve both.  The window test is a predicate, not a branch
+  // (nearly every candidate passes for some lane of a row).  Expressions and the strict
+  // first-index comparison are those of the centre-by-centre sweep.
+  constexpr int kHalf = kTile / 2;
 #pragma unroll
-  for (int pass = 0; pass < kTile / kRowsPerPass; ++pass) {
-    const int x = x0 + lane, y = y0 + warp + kRowsPerPass * pass;
-    const bool inside = x < W && y < H;
-    int lab = -1, slot = -1;
-    long long q = 0;
-    if (inside) {
-      const size_t p = (size_t)y * W + x;
-      const float val = D2[p];
-      lab = labels[p];
-      if (do_assign) {
-        float best = INFINITY;
-        const float fxp = (float)x, fyp = (float)y;
-        if (!overflow) {
-          for (int i = 0; i < nc; ++i) {
-            float fx = fxp - ccx[i];
-            float fy = fyp - ccy[i];
-            if (!(fabsf(fx) <= Sf && fabsf(fy) <= Sf)) continue;
-            float dv = val - ccv[i];
-            float dd = dv * dv + (fx * fx + fy * fy) * coef;
-            if (dd < best) {
-              best = dd;
-              lab = cand[i];
-              slot = i;
-            }
-          }
-        } else {  // rare: too many candidates for shared memory; scan every centre
-          for (int k = 0; k < n; ++k) {
-            float fx = fxp - cx[k];
-            float fy = fyp - cy[k];
-            if (!(fabsf(fx) <= Sf && fabsf(fy) <= Sf)) continue;
-            float dv = val - cv[k];
-            float dd = dv * dv + (fx * fx + fy * fy) * coef;
-            if (dd < best) {
-              best = dd;
-              lab = k;
+  for (int pass = 0; pass < kHalf / kRowsPerPass; ++pass) {
+    const int x = x0 + lane;
+    int yy[2], lab[2], slot[2];
+    bool inside[2];
+    float val[2];
+    long long q[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      yy[h] = y0 + warp + kRowsPerPass * pass + kHalf * h;
+      inside[h] = x < W && yy[h] < H;
+      lab[h] = -1;
+      slot[h] = -1;
+      q[h] = 0;
+      val[h] = 0.0f;
+      if (inside[h]) {
+        const size_t p = (size_t)yy[h] * W + x;
+        val[h] = D2[p];
+        lab[h] = labels[p];
+      }
+    }
+    if (do_assign) {
+      float best[2] = {INFINITY, INFINITY};
+      const float fxp = (float)x;
+      const float fyp[2] = {(float)yy[0], (float)yy[1]};
+      if (!overflow) {
+        for (int i = 0; i < nc; ++i) {
+          const float fx = fxp - ccx[i], cyi = ccy[i], cvi = ccv[i];
+          const bool inx = fabsf(fx) <= Sf;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const float fy = fyp[h] - cyi;
+            const float dv = val[h] - cvi;
+            const float dd = dv * dv + (fx * fx + fy * fy) * coef;
+            if (inx && fabsf(fy) <= Sf && dd < best[h]) {
+              best[h] = dd;
+              slot[h] = i;
             }
           }
         }
-        labels[p] = lab;
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          if (slot[h] >= 0) lab[h] = cand[slot[h]];
+      } else {  // rare: too many candidates for shared memory; scan every centre
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (!inside[h]) continue;
+          for (int k = 0; k < n; ++k) {
+            float fx = fxp - cx[k];
+            float fy = fyp[h] - cy[k];
+            if (!(fabsf(fx) <= Sf && fabsf(fy) <= Sf)) continue;
+            float dv = val[h] - cv[k];
+            float dd = dv * dv + (fx * fx + fy * fy) * coef;
+            if (dd < best[h]) {
+              best[h] = dd;
+              lab[h] = k;
+            }
+          }
+        }
       }
-      q = __float2ll_rn(val * 1024.0f);  // exact scaling; rounds half to even like rint
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        if (inside[h]) labels[(size_t)yy[h] * W + x] = lab[h];
     }
-    // a label's slot is the same for every lane that has it, so grouping by label groups by
-    // slot; lanes that kept an uncovered pixel's old label (slot -1) go straight to the global sums
-    warp_accumulate(inside && slot >= 0, lab, slot, x, y, q, sacc, acc);
-    warp_accumulate(inside && slot < 0, lab, -1, x, y, q, sacc, acc);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (inside[h]) q[h] = __float2ll_rn(val[h] * 1024.0f);  // exact scaling; rint's rounding
+      // a label's slot is the same for every lane that has it, so grouping by label groups by
+      // slot; lanes that kept an uncovered pixel's old label (slot -1) go straight to the global
+      // sums
+      warp_accumulate(inside[h] && slot[h] >= 0, lab[h], slot[h], x, yy[h], q[h], sacc, acc);
+      warp_accumulate(inside[h] && slot[h] < 0, lab[h], -1, x, yy[h], q[h], sacc, acc);
+    }
   }
   __syncthreads();
   if (!overflow)
