@@ -186,20 +186,21 @@ __global__ void __launch_bounds__(kTileThreads) k_slic_assign(
     sacc[i][0] = sacc[i][1] = sacc[i][2] = sacc[i][3] = sacc[i][4] = 0u;
   __syncthreads();
 
-  // A thread takes two pixels per pass, rows y and y + kTile / 2 of its column: each candidate's
-  // shared loads and x distance then serve both.  The window test is a predicate, not a branch
+  // A thread takes NP pixels of its column, kTile / NP rows apart: each candidate's shared loads
+  // and x distance then serve all of them.  The window test is a predicate, not a branch
   // (nearly every candidate passes for some lane of a row).  Expressions and the strict
   // first-index comparison are those of the centre-by-centre sweep.
-  constexpr int kHalf = kTile / 2;
+  constexpr int NP = 4;
+  constexpr int kHalf = kTile / NP;  // row spacing of a thread's pixels
 #pragma unroll
   for (int pass = 0; pass < kHalf / kRowsPerPass; ++pass) {
     const int x = x0 + lane;
-    int yy[2], lab[2], slot[2];
-    bool inside[2];
-    float val[2];
-    long long q[2];
+    int yy[NP], lab[NP], slot[NP];
+    bool inside[NP];
+    float val[NP];
+    long long q[NP];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < NP; ++h) {
       yy[h] = y0 + warp + kRowsPerPass * pass + kHalf * h;
       inside[h] = x < W && yy[h] < H;
       lab[h] = -1;
@@ -213,15 +214,19 @@ __global__ void __launch_bounds__(kTileThreads) k_slic_assign(
       }
     }
     if (do_assign) {
-      float best[2] = {INFINITY, INFINITY};
+      float best[NP], fyp[NP];
+#pragma unroll
+      for (int h = 0; h < NP; ++h) {
+        best[h] = INFINITY;
+        fyp[h] = (float)yy[h];
+      }
       const float fxp = (float)x;
-      const float fyp[2] = {(float)yy[0], (float)yy[1]};
       if (!overflow) {
         for (int i = 0; i < nc; ++i) {
           const float fx = fxp - ccx[i], cyi = ccy[i], cvi = ccv[i];
           const bool inx = fabsf(fx) <= Sf;
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
+          for (int h = 0; h < NP; ++h) {
             const float fy = fyp[h] - cyi;
             const float dv = val[h] - cvi;
             const float dd = dv * dv + (fx * fx + fy * fy) * coef;
@@ -232,11 +237,11 @@ __global__ void __launch_bounds__(kTileThreads) k_slic_assign(
           }
         }
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
+        for (int h = 0; h < NP; ++h)
           if (slot[h] >= 0) lab[h] = cand[slot[h]];
       } else {  // rare: too many candidates for shared memory; scan every centre
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < NP; ++h) {
           if (!inside[h]) continue;
           for (int k = 0; k < n; ++k) {
             float fx = fxp - cx[k];
@@ -252,11 +257,11 @@ __global__ void __launch_bounds__(kTileThreads) k_slic_assign(
         }
       }
 #pragma unroll
-      for (int h = 0; h < 2; ++h)
+      for (int h = 0; h < NP; ++h)
         if (inside[h]) labels[(size_t)yy[h] * W + x] = lab[h];
     }
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < NP; ++h) {
       if (inside[h]) q[h] = __float2ll_rn(val[h] * 1024.0f);  // exact scaling; rint's rounding
       // a label's slot is the same for every lane that has it, so grouping by label groups by
       // slot; lanes that kept an uncovered pixel's old label (slot -1) go straight to the global
