@@ -152,7 +152,7 @@ void launch_batch_wave(cudaStream_t s, const BatchWaveDev& w, int P1, int P2, in
   const int n = w.npairs;
   k_kappa_b<<<w.total[kStageKappa], 128, 0, s>>>(w.pairs, w.starts[kStageKappa], n);
   k_fill_b<<<w.total[kStageFill], 1024, 0, s>>>(w.pairs, w.starts[kStageFill], n);
-  k_census_b<<<2 * w.total[kStageCensus], dim3(kCT_W, kCT_H), 0, s>>>(w.pairs,
+  k_census_b<<<2 * w.total[kStageCensus], dim3(kCT_W, kCT_TY), 0, s>>>(w.pairs,
                                                                      w.starts[kStageCensus], n,
                                                                      w.total[kStageCensus]);
   k_cost_b<<<w.total[kStageCost], kCostThreads, 0, s>>>(w.pairs, w.starts[kStageCost], n);

@@ -224,13 +224,13 @@ void launch_warp(cudaStream_t s, const uint8_t* right, int W, int H, size_t pitc
 void launch_census(cudaStream_t s, const uint8_t* img, int W, int H, size_t pitch,
                    const int32_t* kappa, uint32_t* codes) {
   dim3 grid((W + kCT_W - 1) / kCT_W, (H + kCT_H - 1) / kCT_H);
-  k_census<<<grid, dim3(kCT_W, kCT_H), 0, s>>>(img, W, H, pitch, kappa, codes);
+  k_census<<<grid, dim3(kCT_W, kCT_TY), 0, s>>>(img, W, H, pitch, kappa, codes);
 }
 
 void launch_census_pair(cudaStream_t s, const uint8_t* left, const uint8_t* right, int W, int H,
                         size_t pitch, const int32_t* kappa, uint32_t* cl, uint32_t* cr) {
   dim3 grid((W + kCT_W - 1) / kCT_W, (H + kCT_H - 1) / kCT_H, 2);
-  k_census_pair<<<grid, dim3(kCT_W, kCT_H), 0, s>>>(left, right, W, H, pitch, kappa, cl, cr);
+  k_census_pair<<<grid, dim3(kCT_W, kCT_TY), 0, s>>>(left, right, W, H, pitch, kappa, cl, cr);
 }
 
 void launch_cost(cudaStream_t s, const uint32_t* cl, const uint32_t* cr, int W, int H, int D,

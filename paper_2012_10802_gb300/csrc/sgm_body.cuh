@@ -55,16 +55,17 @@ __device__ __forceinline__ void kappa_row(int W, int H, int order, double a0, do
 }
 
 // ----------------------------------------------------------------------------- census
-constexpr int kCT_W = 32, kCT_H = 8;
+constexpr int kCT_W = 32, kCT_H = 32;  // census tile (pixels)
+constexpr int kCT_TY = 8;              // thread rows of a census block: kCT_H / kCT_TY pixels each
 
-// Census codes of one kCT_W x kCT_H tile (block of kCT_W x kCT_H threads), tile (bx, by).
+// Census codes of one kCT_W x kCT_H tile (block of kCT_W x kCT_TY threads), tile (bx, by).
 __device__ __forceinline__ void census_tile(const uint8_t* __restrict__ img, int W, int H,
                                             size_t pitch, const int32_t* __restrict__ kappa,
                                             uint32_t* __restrict__ codes, int bx, int by) {
   __shared__ uint8_t tile[kCT_H + 4][kCT_W + 4];
-  int u0 = bx * kCT_W, v0 = by * kCT_H;
+  const int u0 = bx * kCT_W, v0 = by * kCT_H;
   for (int i = threadIdx.y * kCT_W + threadIdx.x; i < (kCT_H + 4) * (kCT_W + 4);
-       i += kCT_W * kCT_H) {
+       i += kCT_W * kCT_TY) {
     int ty = i / (kCT_W + 4), tx = i % (kCT_W + 4);
     int y = clampi(v0 + ty - 2, 0, H - 1);
     int x = clampi(u0 + tx - 2, 0, W - 1);
@@ -72,20 +73,25 @@ __device__ __forceinline__ void census_tile(const uint8_t* __restrict__ img, int
     tile[ty][tx] = img[(size_t)y * pitch + x];
   }
   __syncthreads();
-  int u = u0 + threadIdx.x, v = v0 + threadIdx.y;
-  if (u >= W || v >= H) return;
-  uint8_t c = tile[threadIdx.y + 2][threadIdx.x + 2];
-  uint32_t code = 0;
-  int k = 0;
+  const int u = u0 + threadIdx.x;
+  if (u >= W) return;
 #pragma unroll
-  for (int dy = 0; dy < 5; ++dy)
+  for (int r = 0; r < kCT_H / kCT_TY; ++r) {
+    const int ly = threadIdx.y + kCT_TY * r, v = v0 + ly;
+    if (v >= H) break;
+    const uint8_t c = tile[ly + 2][threadIdx.x + 2];
+    uint32_t code = 0;
+    int k = 0;
 #pragma unroll
-    for (int dx = 0; dx < 5; ++dx) {
-      if (dx == 2 && dy == 2) continue;
-      code |= (uint32_t)(tile[threadIdx.y + dy][threadIdx.x + dx] < c) << k;
-      ++k;
-    }
-  codes[(size_t)v * W + u] = code;
+    for (int dy = 0; dy < 5; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 5; ++dx) {
+        if (dx == 2 && dy == 2) continue;
+        code |= (uint32_t)(tile[ly + dy][threadIdx.x + dx] < c) << k;
+        ++k;
+      }
+    codes[(size_t)v * W + u] = code;
+  }
 }
 
 // ----------------------------------------------------------------------------- cost
