@@ -83,6 +83,15 @@ inline size_t carve_size(size_t& acc, size_t n) {
   return acc;
 }
 
+// Key whose signed order is the order of the doubles (NaN excluded; -0 is folded to +0, so
+// equal values tie): minimum searches compare it with integer instructions instead of FP64
+// compares, which take about 63 cycles each on GB300.
+__device__ __forceinline__ long long f64_order_key(double e) {
+  long long b = __double_as_longlong(e);
+  if (b == (long long)0x8000000000000000ULL) b = 0;
+  return b < 0 ? (b ^ 0x7fffffffffffffffLL) : b;
+}
+
 // Raises kernel f's dynamic shared-memory limit to at least `bytes` on the current device.  The
 // limit belongs to the device's context, so it is tracked per (kernel, device); repeated calls
 // cost a lookup.

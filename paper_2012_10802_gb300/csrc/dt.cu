@@ -268,13 +268,6 @@ struct RollFit {
   double c, s, beta[3];
 };
 
-// Key whose signed order is the order of the doubles (no NaN occurs: a failed fit is +inf);
-// -0 is folded to +0, so equal energies still tie and the smaller index wins.
-__device__ __forceinline__ long long energy_key(double e) {
-  long long b = __double_as_longlong(e);
-  if (b == (long long)0x8000000000000000ULL) b = 0;
-  return b < 0 ? (b ^ 0x7fffffffffffffffLL) : b;
-}
 
 // Converts the 22 sums (after the count) to doubles, one per lane of the calling warp; the caller
 // synchronises before reading M.
@@ -380,7 +373,7 @@ __global__ void __launch_bounds__(kRollWarp) k_roll_grid(const int64_t* __restri
     e = e0min_cs(M, order, coord_scale_d(W, H), cp, sp, beta);
   }
   int kk = k < kGridN ? k : 0x7fffffff;
-  long long key = energy_key(e);
+  long long key = f64_order_key(e);
   warp_argmin(key, kk);
   if (threadIdx.x == 0) res[blockIdx.x] = RollBest{key, kk, 0};
 }
@@ -409,7 +402,7 @@ __global__ void __launch_bounds__(kRollWarp) k_roll_round(const int64_t* __restr
   const double cphi = ca * ct - sa * st, sphi = sa * ct + ca * st;
   double e = e0min_cs(M, order, coord_scale_d(W, H), cphi, sphi, beta);
   int k = i;
-  long long key = energy_key(e);
+  long long key = f64_order_key(e);
   warp_argmin(key, k);
   if (threadIdx.x == 0)
     res[kGridBlocks + (round - 1) * kRoundBlocks + blockIdx.x] = RollBest{key, k, 0};
