@@ -133,6 +133,20 @@ def test_sgm_fused_bit_exact(orc, B, ctx, W, H, D, paths):
     assert np.array_equal(host(D1), ref["D1"])
 
 
+@pytest.mark.parametrize("P1,P2", [(4, 32), (7, 39), (8, 40), (10, 64), (1, 231)])
+@pytest.mark.parametrize("D", [64, 128])
+def test_sgm_fused_penalty_sweep(orc, B, ctx, P1, P2, D):
+    """The fused path over penalties up to the largest P2 whose L still fits a byte (24 + P2 =
+    255): every L volume and the disparities stay exact."""
+    sc, left, right = pair(200, 96, 13)
+    p = orc.Params(D=D, paths=8, P1=P1, P2=P2)
+    ref = orc.sgm(left, right, omodel(orc, sc), p)
+    params = B.default_params(D=D, paths=8, P1=P1, P2=P2)
+    kap, d_int, D1 = B.pd_sgm(ctx, dev(left), dev(right), bmodel(B, sc), params)
+    assert np.array_equal(host(d_int), ref["d_int"])
+    assert np.array_equal(host(D1), ref["D1"])
+
+
 @pytest.mark.slow
 def test_sgm_fused_bit_exact_720p_d128(orc, B, ctx):
     """The benchmark workload itself: 1280x720, D = 128, 8 paths, in the launch configuration the
