@@ -291,11 +291,24 @@ __global__ void k_slic_update(int n, unsigned long long* __restrict__ acc, float
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   unsigned long long* a = acc + 4 * (size_t)k;
-  long long cnt = (long long)a[0];
+  const long long cnt = (long long)a[0];
+  const long long sx = (long long)a[1], sy = (long long)a[2], sq = (long long)a[3];
   if (cnt > 0) {
-    cx[k] = (float)((double)(long long)a[1] / (double)cnt);
-    cy[k] = (float)((double)(long long)a[2] / (double)cnt);
-    cv[k] = (float)(((double)(long long)a[3] / (double)cnt) / 1024.0);
+    const long long lim = 1LL << 24;
+    if (cnt < lim && sx > -lim && sx < lim && sy > -lim && sy < lim && sq > -lim && sq < lim) {
+      // Every operand is an exact float, so the correctly rounded float quotient equals the
+      // double quotient rounded to float (double has at least 2 x 24 + 2 bits, which makes the
+      // double rounding innocuous for a division), and /1024 scales exactly: the FP32 pipe
+      // gives the result of the double expressions below without the slow FP64 one.
+      const float fc = (float)(int)cnt;
+      cx[k] = __fdiv_rn((float)(int)sx, fc);
+      cy[k] = __fdiv_rn((float)(int)sy, fc);
+      cv[k] = __fdiv_rn((float)(int)sq, fc) * (1.0f / 1024.0f);
+    } else {
+      cx[k] = (float)((double)sx / (double)cnt);
+      cy[k] = (float)((double)sy / (double)cnt);
+      cv[k] = (float)(((double)sq / (double)cnt) / 1024.0);
+    }
   }
   a[0] = a[1] = a[2] = a[3] = 0ULL;
 }
