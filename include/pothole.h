@@ -365,7 +365,8 @@ pd_status pd_sgm_band(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, in
  * (an extension beyond the paper; it restates no passage of it).  Input x: bf16 [B][Hd][Wd][2],
  * Hd = ceil(H/4), Wd = ceil(W/4), as written by pd_band_input.  Four 3x3 convolutions with zero
  * padding 1, strides 1, 2, 2, 1 and channels 2 -> 32 -> 32 -> 32 -> 2, ReLU after the first three;
- * bf16 operands, fp32 accumulation, bf16 activations.  Output out: float [B][Ho][Wo][2] with
+ * bf16 operands, fp32 accumulation, bf16 activations (each forward convolution an implicit GEMM on
+ * the tensor cores with the accumulator in tensor memory).  Output out: float [B][Ho][Wo][2] with
  * Ho = ceil(Hd/4) = ceil(H/16) (likewise Wo): channel 0 = centre / 16 (pixels of the shifted
  * pair), channel 1 = logit of the confidence that the tile's disparities lie within +-7 of it.
  * Parameters: 19682 floats, per layer the weights [Cout][3][3][Cin] then the Cout biases. */
@@ -385,6 +386,16 @@ pd_status pd_cnn_get_params(pd_ctx* ctx, pd_cnn* net, float* host_params, int n)
 /* Forward pass; x and out are device pointers (layouts above). */
 pd_status pd_cnn_forward(pd_ctx* ctx, pd_cnn* net, const void* x, int B, int Hd, int Wd,
                          float* out);
+
+/* The convolutions run on the fifth-generation tensor cores: one thread per CTA issues the MMAs
+ * into tensor memory and every thread waits for their completion on an mbarrier, for about a
+ * second at most.  A wait that runs out sets a flag in the network instead of hanging the device.
+ * pd_cnn_check synchronises ctx's stream and returns PD_ERR_TIMEOUT (and clears the flag) if any
+ * call since the last check saw a wait run out, else PD_OK.  pd_cnn_probe_timeout enqueues one
+ * convolution CTA that issues no MMA, so that its wait runs out after limit_cycles SM clock cycles
+ * (0 .. 2^31): the timeout path itself, for tests. */
+pd_status pd_cnn_check(pd_ctx* ctx, pd_cnn* net);
+pd_status pd_cnn_probe_timeout(pd_ctx* ctx, pd_cnn* net, long long limit_cycles);
 
 /* Loss and its gradient with respect to the parameters.  targets: float [B][Ho][Wo][4] = (centre
  * in pixels, confidence label 0/1, centre weight, confidence weight).  Loss = sum of centre

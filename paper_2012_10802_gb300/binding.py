@@ -103,6 +103,8 @@ SIGNATURES = {
     "pd_cnn_forward": [_P, _P, _P, _i, _i, _i, _P],
     "pd_cnn_loss_grad": [_P, _P, _P, _P, _i, _i, _i, _P, _P],
     "pd_cnn_train_step": [_P, _P, _P, _P, _i, _i, _i, _f, _P],
+    "pd_cnn_check": [_P, _P],
+    "pd_cnn_probe_timeout": [_P, _P, C.c_longlong],
     "pd_band_input": [_P, _P, _P, _i, _i, _z, _P, _P],
     "pd_band_labels": [_P, _P, _P, _i, _i, _i, _P],
     "pd_band_tiles": [_P, _P, _i, _i, _i, _i, _P],
@@ -391,6 +393,16 @@ def pd_cnn_forward(ctx, net, x, out=None):
         out = ctx.empty((B, Ho, Wo, 2), torch.float32)
     ctx.check(lib().pd_cnn_forward(ctx.h, net.h, _ptr(x), B, Hd, Wd, _ptr(out)))
     return out
+
+
+def pd_cnn_check(ctx, net):
+    """Synchronises; raises PdError (PD_ERR_TIMEOUT) if a tensor-core wait of the network ran out
+    since the last check."""
+    ctx.check(lib().pd_cnn_check(ctx.h, net.h))
+
+
+def pd_cnn_probe_timeout(ctx, net, limit_cycles):
+    ctx.check(lib().pd_cnn_probe_timeout(ctx.h, net.h, int(limit_cycles)))
 
 
 def pd_cnn_loss_grad(ctx, net, x, targets):

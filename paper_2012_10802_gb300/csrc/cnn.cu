@@ -4,11 +4,12 @@
 //
 // Network: 3x3 convolutions, zero padding 1, strides 1, 2, 2, 1, channels 2 -> 32 -> 32 -> 32 -> 2,
 // ReLU after the first three, on the 4x-block-averaged row-shifted pair.  Activations are bf16,
-// NHWC; each convolution is an explicit im2col (k = (ky * 3 + kx) * Cin + ci) followed by a bf16
-// tensor-core GEMM with fp32 accumulation (mma.m16n8k16, operands staged in shared memory and
-// loaded with ldmatrix).  The backward pass uses the same GEMM with transposed operand layouts:
-// dW = dZ^T Col (split over pixels, fp32 atomics), dCol = dZ W, and a gather col2im that applies
-// the previous layer's ReLU mask.  Training is Adam on fp32 master weights.
+// NHWC.  Every contraction runs on the fifth-generation tensor cores (bf16 operands in shared
+// memory, fp32 accumulators in tensor memory, one issuing thread per CTA): each convolution is an
+// implicit GEMM over the patch matrix (k = (ky * 3 + kx) * Cin + ci), and the backward pass computes
+// dW = dZ^T Col (split over pixels, fp32 atomics) and dCol = dZ W with operands read in place
+// (MN-major where the contraction runs along their rows), then a gather col2im that applies the
+// previous layer's ReLU mask.  Training is Adam on fp32 master weights.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -18,217 +19,415 @@
 #include <cuda_bf16.h>
 
 #include "common.cuh"
+#include "tcgen05.cuh"
 
 namespace pd {
 
 namespace {
 
-// ------------------------------------------------------------------------------- GEMM
-// C[M][N] = sum_k A(m, k) B(k, n), A and B bf16, fp32 accumulation.
-//   A_ROW: A stored [M][lda] (k contiguous); otherwise [K][lda] (m contiguous).
-//   B_NK:  B stored [N][ldb] (k contiguous); otherwise [K][ldb] (n contiguous).
-// Contiguous extents must be multiples of 8 elements and rows 16-byte aligned; out-of-range
-// rows and 8-element groups are read as zeros.  blockIdx.z splits K into chunks of k_chunk.
-constexpr int kBM = 64, kBN = 32, kBK = 32, kGemmThreads = 128;
-constexpr int kPad = 8;  // bf16 elements of padding per shared-memory row (bank spread)
+// ------------------------------------------------------------------- convolution on tcgen05
+// One CTA computes 128 output pixels x all output channels of a 3x3 convolution (zero padding 1)
+// as an implicit GEMM with K = Kp (k = (ky * 3 + kx) * Cin + ci, zeros up to Kp):
+//  * the 128 x Kp patch matrix is gathered straight from the NHWC input into shared memory in
+//    the K-major core-matrix layout (rows 8 r8 .. 8 r8 + 7 of k-group g at g * 2048 + r8 * 128
+//    bytes), the weights [CoutP][Kp] likewise with N rows (rows >= CoutP zero), and the bias;
+//  * one thread issues Kp / 16 MMAs of 128 x N x 16 into a TMEM accumulator of N fp32 columns and
+//    commits them to an mbarrier, which every thread waits on (bounded);
+//  * warp w reads rows 32 (w mod 4) .. + 31, columns 8 (w / 4) .. + 7 back, adds the bias and
+//    stores bf16 [P][32] after ReLU (hidden layers) or fp32 [P][2] (output layer, N = 16).
+// 16 warps per CTA: the grids of the later layers are small (64 CTAs at 1080p), so each CTA's
+// gather and read-back are spread over as many threads as it has (row, 8-channel) pieces.
+// With WRITE_COL the gathered patches also go to Col [P][Kp] for the backward pass.
+constexpr int kConvM = 128, kConvThreads = 512;
+constexpr long long kConvWaitCycles = 1ll << 31;  // about a second at the SM clock
 
-enum Epilogue { kEpiBiasReluBf16 = 0, kEpiBiasF32 = 1, kEpiF32 = 2, kEpiAtomicF32 = 3 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t r[4]) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(addr));
-}
-
-__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t r[4]) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(addr));
-}
-
-__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-struct GemmArgs {
-  const __nv_bfloat16* A;
-  const __nv_bfloat16* B;
-  void* C;
-  const float* bias;
-  int M, N, K, lda, ldb, ldc;
-  int n_store;  // columns written (<= N)
-  int k_chunk;
+struct ConvArgs {
+  const __nv_bfloat16* X;  // [B][H][W][Cin]
+  int B, H, W, Ho, Wo, stride;
+  const __nv_bfloat16* Wt;  // [coutp][Kp]
+  int coutp;
+  const float* bias;  // [32], 16-byte aligned
+  void* out;
+  __nv_bfloat16* col;
+  int* status;  // bit 0 set when the MMA wait ran out
+  int P;        // B * Ho * Wo (< 2^31 / 36 by the network's size limit)
+  long long wait_limit;
+  int issue;  // 0 issues no MMA, so that the wait runs out (the timeout path's test)
 };
 
-template <bool A_ROW, bool B_NK, int EPI>
-__global__ void __launch_bounds__(kGemmThreads) k_gemm(GemmArgs g) {
-  // A tile: A_ROW ? [kBM][kBK + kPad] : [kBK][kBM + kPad];  B tile: B_NK ? [kBN][kBK + kPad] : [kBK][kBN + kPad]
-  __shared__ __align__(16) __nv_bfloat16 sA[kBM * (kBK + kPad) > kBK * (kBM + kPad) ? kBM * (kBK + kPad) : kBK * (kBM + kPad)];
-  __shared__ __align__(16) __nv_bfloat16 sB[kBN * (kBK + kPad) > kBK * (kBN + kPad) ? kBN * (kBK + kPad) : kBK * (kBN + kPad)];
+__host__ __device__ constexpr int conv_kp(int cin) { return cin == 32 ? 288 : 32; }
+
+// Dynamic shared memory of one CTA: the patch tile, the weight tile, the bias.
+constexpr size_t conv_smem_bytes(int cin, int n) {
+  return (size_t)(conv_kp(cin) / 8) * (kConvM + n) * 16 + 32 * sizeof(float);
+}
+
+template <int CIN, int N, bool F32OUT, bool WRITE_COL>
+__global__ void __launch_bounds__(kConvThreads) k_conv_tc(ConvArgs a) {
+  constexpr int KP = conv_kp(CIN), KG = KP / 8;
+  constexpr uint32_t kGroupA = kConvM * 16, kGroupB = N * 16;  // bytes per k-group
+  constexpr uint32_t kCols = N < 32 ? 32 : N;
+  extern __shared__ __align__(128) uint8_t conv_smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
-  const int k_begin = blockIdx.z * g.k_chunk;
-  const int k_end = min(g.K, k_begin + g.k_chunk);
-  float acc[4][4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) acc[j][i] = 0.0f;
+  const int m0 = blockIdx.x * kConvM;
+  const uint32_t sA = tc::smem_addr(conv_smem), sB = sA + KG * kGroupA;
+  const uint32_t sBias = sB + KG * kGroupB;
+  const float* bias_s = reinterpret_cast<const float*>(conv_smem + KG * kGroupA + KG * kGroupB);
+  const uint32_t bar = tc::smem_addr(&mbar);
+  if (warp == 0) tc::tmem_alloc(tc::smem_addr(&tslot), kCols);
+  if (tid == 0) tc::mbar_init(bar, 1);
 
-  for (int k0 = k_begin; k0 < k_end; k0 += kBK) {
-    // ---- stage A (kBM x kBK = 256 vectors of 8) and B (kBN x kBK = 128 vectors)
+  for (int c = tid; c < KG * N; c += kConvThreads) {
+    const int n = c % N, g = c / N;
+    const bool ok = n < a.coutp;
+    tc::cp_async16(sB + g * kGroupB + n * 16, a.Wt + (ok ? n * KP + g * 8 : 0), ok ? 16u : 0u);
+  }
+  if (tid < 8) tc::cp_async16(sBias + tid * 16, a.bias + tid * 4, 16u);
+  if (CIN == 32) {
+    // thread: channel quarter q of row tid / 4, all 9 taps (4 lanes read one 64-byte pixel)
+    const int q = tid & 3, row = tid >> 2;
+    const int p = m0 + row;
+    const bool vp = p < a.P;
+    int b = 0, oy = 0, ox = 0;
+    if (vp) {
+      ox = p % a.Wo;
+      const int t = p / a.Wo;
+      oy = t % a.Ho;
+      b = t / a.Ho;
+    }
+    const int y0 = oy * a.stride - 1, x0 = ox * a.stride - 1;
+    const __nv_bfloat16* base = a.X + ((size_t)b * a.H * a.W) * 32 + q * 8;
 #pragma unroll
-    for (int it = 0; it < 2; ++it) {
-      const int vi = tid + it * kGemmThreads;
-      uint4 val = make_uint4(0, 0, 0, 0);
-      if (A_ROW) {
-        const int r = vi >> 2, c = (vi & 3) * 8;  // row m0 + r, k0 + c .. + 7
-        const int m = m0 + r, k = k0 + c;
-        if (m < g.M && k < k_end)
-          val = *reinterpret_cast<const uint4*>(g.A + (size_t)m * g.lda + k);
-        *reinterpret_cast<uint4*>(sA + r * (kBK + kPad) + c) = val;
+    for (int tap = 0; tap < 9; ++tap) {
+      const int y = y0 + tap / 3, x = x0 + tap % 3;
+      const bool ok = vp && y >= 0 && y < a.H && x >= 0 && x < a.W;
+      const __nv_bfloat16* src = ok ? base + ((size_t)y * a.W + x) * 32 : a.X;
+      const uint32_t off = (tap * 4 + q) * kGroupA + row * 16;
+      if (WRITE_COL) {
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (ok) v = *reinterpret_cast<const uint4*>(src);
+        *reinterpret_cast<uint4*>(conv_smem + off) = v;
+        if (vp) *reinterpret_cast<uint4*>(a.col + (size_t)p * KP + tap * 32 + q * 8) = v;
       } else {
-        const int r = vi >> 3, c = (vi & 7) * 8;  // k row k0 + r, m0 + c .. + 7
-        const int k = k0 + r, m = m0 + c;
-        if (k < k_end && m < g.M)
-          val = *reinterpret_cast<const uint4*>(g.A + (size_t)k * g.lda + m);
-        *reinterpret_cast<uint4*>(sA + r * (kBM + kPad) + c) = val;
+        tc::cp_async16(sA + off, src, ok ? 16u : 0u);
       }
     }
-    {
-      const int vi = tid;
-      uint4 val = make_uint4(0, 0, 0, 0);
-      if (B_NK) {
-        const int r = vi >> 2, c = (vi & 3) * 8;
-        const int n = n0 + r, k = k0 + c;
-        if (n < g.N && k < k_end)
-          val = *reinterpret_cast<const uint4*>(g.B + (size_t)n * g.ldb + k);
-        *reinterpret_cast<uint4*>(sB + r * (kBK + kPad) + c) = val;
-      } else {
-        const int r = vi >> 2, c = (vi & 3) * 8;
-        const int k = k0 + r, n = n0 + c;
-        if (k < k_end && n < g.N)
-          val = *reinterpret_cast<const uint4*>(g.B + (size_t)k * g.ldb + n);
-        *reinterpret_cast<uint4*>(sB + r * (kBN + kPad) + c) = val;
-      }
+  } else {
+    // Cin = 2: thread = (row, k-group g); g holds taps 4 g .. 4 g + 3 (two channels each), taps
+    // >= 9 are zero; one 16-byte shared store per thread (consecutive rows, consecutive bytes)
+    const int row = tid & 127, g = tid >> 7;
+    const int p = m0 + row;
+    const bool vp = p < a.P;
+    int b = 0, oy = 0, ox = 0;
+    if (vp) {
+      ox = p % a.Wo;
+      const int t = p / a.Wo;
+      oy = t % a.Ho;
+      b = t / a.Ho;
     }
-    __syncthreads();
+    const uint32_t* img = reinterpret_cast<const uint32_t*>(a.X) + (size_t)b * a.H * a.W;
+    uint32_t v[4];
 #pragma unroll
-    for (int kk = 0; kk < kBK; kk += 16) {
-      uint32_t a[4];
-      const int wm = warp * 16;
-      if (A_ROW) {
-        const int r = wm + (lane & 15), c = kk + (lane >> 4) * 8;
-        ldsm_x4(smem_u32(sA + r * (kBK + kPad) + c), a);
-      } else {
-        const int q = lane >> 3, i = lane & 7;  // matrix q: m half q & 1, k half q >> 1
-        const int r = kk + (q >> 1) * 8 + i, c = wm + (q & 1) * 8;
-        ldsm_x4_t(smem_u32(sA + r * (kBM + kPad) + c), a);
-      }
+    for (int t4 = 0; t4 < 4; ++t4) {
+      const int tap = 4 * g + t4;
+      const int y = oy * a.stride + tap / 3 - 1, x = ox * a.stride + tap % 3 - 1;
+      const bool ok = vp && tap < 9 && y >= 0 && y < a.H && x >= 0 && x < a.W;
+      v[t4] = ok ? img[(size_t)y * a.W + x] : 0u;
+    }
+    const uint4 u = make_uint4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<uint4*>(conv_smem + g * kGroupA + row * 16) = u;
+    if (WRITE_COL && vp) *reinterpret_cast<uint4*>(a.col + (size_t)p * KP + g * 8) = u;
+  }
+  tc::cp_async_wait_all();
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = tslot;
+
+  if (tid == 0 && a.issue) {
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(kConvM, N);
+#pragma unroll 1
+    for (int ks = 0; ks < KP / 16; ++ks) {
+      const uint64_t ad = tc::smem_desc(sA + ks * 2 * kGroupA, kGroupA, 128);
+      const uint64_t bd = tc::smem_desc(sB + ks * 2 * kGroupB, kGroupB, 128);
+      tc::mma_bf16(taddr, ad, bd, idesc, ks > 0 ? 1u : 0u);
+    }
+    tc::mma_commit(bar);
+  }
+  const bool done = __all_sync(0xffffffffu, tc::mbar_wait_bounded(bar, 0, a.wait_limit));
+  tc::fence_after_sync();
+  const int quarter = warp & 3, cblk = warp >> 2;  // lanes 32 quarter .., columns 8 cblk ..
+  if (!done) {
+    if (lane == 0) atomicOr(a.status, 1);
+  } else if (8 * cblk < N) {
+    uint32_t r[8];
+    tc::tmem_ld8(taddr + ((uint32_t)(quarter * 32) << 16) + 8 * cblk, r);
+    const int p = m0 + quarter * 32 + lane;
+    if (p < a.P) {
+      if (!F32OUT) {
+        uint32_t h[4];
 #pragma unroll
-      for (int jp = 0; jp < 2; ++jp) {  // n tiles 2 jp and 2 jp + 1
-        uint32_t b[4];
-        const int q = lane >> 3, i = lane & 7;
-        if (B_NK) {  // matrices: (n tile 2jp, k lo), (2jp, k hi), (2jp+1, k lo), (2jp+1, k hi)
-          const int r = jp * 16 + (q >> 1) * 8 + i, c = kk + (q & 1) * 8;
-          ldsm_x4(smem_u32(sB + r * (kBK + kPad) + c), b);
-        } else {
-          const int r = kk + (q & 1) * 8 + i, c = jp * 16 + (q >> 1) * 8;
-          ldsm_x4_t(smem_u32(sB + r * (kBN + kPad) + c), b);
+        for (int i = 0; i < 4; ++i) {
+          const int n = 8 * cblk + 2 * i;
+          const float v0 = fmaxf(__uint_as_float(r[2 * i]) + bias_s[n], 0.0f);
+          const float v1 = fmaxf(__uint_as_float(r[2 * i + 1]) + bias_s[n + 1], 0.0f);
+          const __nv_bfloat162 t = __floats2bfloat162_rn(v0, v1);
+          h[i] = *reinterpret_cast<const uint32_t*>(&t);
         }
-        mma_bf16(acc[2 * jp], a, b[0], b[1]);
-        mma_bf16(acc[2 * jp + 1], a, b[2], b[3]);
+        *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.out) + (size_t)p * 32 +
+                                  8 * cblk) = make_uint4(h[0], h[1], h[2], h[3]);
+      } else if (cblk == 0) {
+        reinterpret_cast<float2*>(a.out)[p] = make_float2(__uint_as_float(r[0]) + bias_s[0],
+                                                          __uint_as_float(r[1]) + bias_s[1]);
       }
     }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    // after a timeout the MMAs may still be running: give them another bounded wait
+    if (!done && a.issue) tc::mbar_wait_bounded(bar, 0, a.wait_limit);
+    tc::tmem_dealloc(taddr, kCols);
+  }
+}
+
+template <int CIN, int N, bool F32OUT, bool WRITE_COL>
+void conv_tc(cudaStream_t s, const ConvArgs& a) {
+  const size_t smem = conv_smem_bytes(CIN, N);
+  raise_smem_limit((const void*)k_conv_tc<CIN, N, F32OUT, WRITE_COL>, smem);
+  const unsigned blocks = (unsigned)((a.P + kConvM - 1) / kConvM);
+  k_conv_tc<CIN, N, F32OUT, WRITE_COL><<<blocks ? blocks : 1, kConvThreads, smem, s>>>(a);
+}
+
+// ----------------------------------------------------------------- backward GEMMs on tcgen05
+constexpr int kBwdThreads = 256;
+
+// dCol[p][k] = sum_co dZ[p][co] W[co][k] (layers 2-4, Kp = 288).  One CTA per 128 pixels:
+//  * A = dZ rows, K-major (co-group g of row r at g * 2048 + r * 16); co-groups beyond ldz zero;
+//  * B = W read MN-major: a core-matrix row is 8 consecutive k of one co, k-group ng and co-group
+//    cg at ng * 512 + cg * 128 (no transpose on the way in);
+//  * K = CoutP (32, or 16 with co >= 8 zero for the output layer); N = 288 as two MMAs of 144
+//    columns into a 512-column accumulator; 8 warps read back 144 columns each.
+struct DcolArgs {
+  const __nv_bfloat16* dZ;  // [P][ldz]
+  int ldz;                  // 32, or 8 for the output layer
+  const __nv_bfloat16* Wt;  // [coutp][288]
+  int coutp;
+  float* dcol;  // [P][288]
+  int* status;
+  int P;
+  long long wait_limit;
+};
+
+constexpr size_t dcol_smem_bytes() { return 4 * (size_t)kConvM * 16 + 36 * 512; }
+
+__global__ void __launch_bounds__(kBwdThreads) k_dcol_tc(DcolArgs a) {
+  constexpr int KP = 288, NG = KP / 8, KC = 32;
+  constexpr uint32_t kGroupA = kConvM * 16, kNGroup = (KC / 8) * 128;
+  extern __shared__ __align__(128) uint8_t bwd_smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * kConvM;
+  const uint32_t sA = tc::smem_addr(bwd_smem), sB = sA + (KC / 8) * kGroupA;
+  const uint32_t bar = tc::smem_addr(&mbar);
+  if (warp == 0) tc::tmem_alloc(tc::smem_addr(&tslot), 512);
+  if (tid == 0) tc::mbar_init(bar, 1);
+  const int ksteps = a.coutp > 8 ? 2 : 1;
+  for (int c = tid; c < kConvM * (KC / 8); c += kBwdThreads) {
+    const int row = c & 127, g = c >> 7;
+    const int p = m0 + row;
+    const bool ok = p < a.P && g * 8 < a.ldz;
+    tc::cp_async16(sA + g * kGroupA + row * 16, a.dZ + (ok ? (size_t)p * a.ldz + g * 8 : 0),
+                   ok ? 16u : 0u);
+  }
+  for (int c = tid; c < NG * KC; c += kBwdThreads) {
+    const int ng = c % NG, co = c / NG;
+    const bool ok = co < a.coutp;
+    tc::cp_async16(sB + ng * kNGroup + (co >> 3) * 128 + (co & 7) * 16,
+                   a.Wt + (ok ? co * KP + ng * 8 : 0), ok ? 16u : 0u);
+  }
+  tc::cp_async_wait_all();
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = tslot;
+  if (tid == 0) {
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(kConvM, 144, false, true);
+    for (int j = 0; j < ksteps; ++j)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint64_t ad = tc::smem_desc(sA + j * 2 * kGroupA, kGroupA, 128);
+        const uint64_t bd = tc::smem_desc(sB + 18 * h * kNGroup + j * 2 * 128, 128, kNGroup);
+        tc::mma_bf16(taddr + 144 * h, ad, bd, idesc, j > 0 ? 1u : 0u);
+      }
+    tc::mma_commit(bar);
+  }
+  const bool done = __all_sync(0xffffffffu, tc::mbar_wait_bounded(bar, 0, a.wait_limit));
+  tc::fence_after_sync();
+  if (!done) {
+    if (lane == 0) atomicOr(a.status, 1);
+  } else {
+    const int quarter = warp & 3, half = warp >> 2;
+    const int p = m0 + quarter * 32 + lane;
+    const uint32_t trow = taddr + ((uint32_t)(quarter * 32) << 16) + 144 * half;
+    float4* dst = reinterpret_cast<float4*>(a.dcol + (size_t)p * KP + 144 * half);
+#pragma unroll 1
+    for (int i = 0; i < 9; ++i) {
+      uint32_t r[16];
+      tc::tmem_ld16(trow + 16 * i, r);
+      if (p < a.P) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          dst[4 * i + v] = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
+                                       __uint_as_float(r[4 * v + 2]),
+                                       __uint_as_float(r[4 * v + 3]));
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    if (!done) tc::mbar_wait_bounded(bar, 0, a.wait_limit);
+    tc::tmem_dealloc(taddr, 512);
+  }
+}
+
+// dW[co][k] += sum over one pixel range of Col[p][k] dZ[p][co].  Grid: (pixel ranges, k-tiles of
+// 128); the CTA accumulates D[k][co] in TMEM over 64-pixel stages and adds it to dW with atomics.
+//  * A = Col read MN-major: a core-matrix row is 8 consecutive k of one pixel, k-group kg and
+//    pixel-group pg of a stage at kg * 1024 + pg * 128;
+//  * B = dZ read MN-major likewise (co-groups; those beyond ldz zero);
+//  * two stage buffers: each is refilled once the commit of the MMAs that read it has arrived.
+struct DwArgs {
+  const __nv_bfloat16* col;  // [P][kp]
+  int kp;                    // 32 or 288
+  const __nv_bfloat16* dZ;   // [P][ldz]
+  int ldz;
+  float* dW;  // [coutp][kp], accumulated
+  int coutp;
+  int* status;
+  int P, chunk;  // pixels per CTA, a multiple of 64
+  long long wait_limit;
+};
+
+constexpr int kDwStage = 64;
+constexpr size_t dw_smem_bytes(int n) { return 2 * (size_t)(16 + n / 8) * 1024; }
+
+template <int N>  // co columns: 32, or 16 for the output layer
+__global__ void __launch_bounds__(kBwdThreads) k_dw_tc(DwArgs a) {
+  constexpr uint32_t kStageA = 16 * 1024, kStageB = (N / 8) * 1024;
+  extern __shared__ __align__(128) uint8_t bwd_smem[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tslot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int k0 = blockIdx.y * 128;
+  const int p_begin = blockIdx.x * a.chunk, p_end = min(a.P, p_begin + a.chunk);
+  const int stages = (p_end - p_begin + kDwStage - 1) / kDwStage;
+  const uint32_t s0 = tc::smem_addr(bwd_smem);
+  if (warp == 0) tc::tmem_alloc(tc::smem_addr(&tslot), 32);
+  if (tid == 0) {
+    tc::mbar_init(tc::smem_addr(&mbar[0]), 1);
+    tc::mbar_init(tc::smem_addr(&mbar[1]), 1);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = tslot;
+  constexpr uint32_t idesc = tc::idesc_bf16_f32(128, N, true, true);
+  bool ok = true;
+  int last = -1;  // last stage whose MMAs were committed
+  for (int s = 0; s < stages; ++s) {
+    const int buf = s & 1;
+    if (s >= 2) {
+      const bool w = tc::mbar_wait_bounded(tc::smem_addr(&mbar[buf]), ((s >> 1) - 1) & 1,
+                                           a.wait_limit);
+      if (__syncthreads_or(!w)) {
+        ok = false;
+        break;
+      }
+    }
+    const uint32_t sa = s0 + buf * (kStageA + kStageB), sb = sa + kStageA;
+    const int ps = p_begin + s * kDwStage;
+    for (int c = tid; c < kDwStage * 16; c += kBwdThreads) {
+      const int kg = 4 * (c >> 8) + (c & 3), pl = (c >> 2) & 63;
+      const int p = ps + pl, k = k0 + kg * 8;
+      const bool okc = p < p_end && k < a.kp;
+      tc::cp_async16(sa + kg * 1024 + pl * 16, a.col + (okc ? (size_t)p * a.kp + k : 0),
+                     okc ? 16u : 0u);
+    }
+    for (int c = tid; c < kDwStage * (N / 8); c += kBwdThreads) {
+      const int cg = c % (N / 8), pl = c / (N / 8);
+      const int p = ps + pl;
+      const bool okc = p < p_end && cg * 8 < a.ldz;
+      tc::cp_async16(sb + cg * 1024 + pl * 16, a.dZ + (okc ? (size_t)p * a.ldz + cg * 8 : 0),
+                     okc ? 16u : 0u);
+    }
+    tc::cp_async_wait_all();
+    tc::fence_async_smem();
+    tc::fence_before_sync();
     __syncthreads();
+    tc::fence_after_sync();
+    if (tid == 0) {
+#pragma unroll
+      for (int j = 0; j < kDwStage / 16; ++j)
+        tc::mma_bf16(taddr, tc::smem_desc(sa + j * 256, 128, 1024),
+                     tc::smem_desc(sb + j * 256, 128, 1024), idesc, (s > 0 || j > 0) ? 1u : 0u);
+      tc::mma_commit(tc::smem_addr(&mbar[buf]));
+    }
+    last = s;
   }
-
-  // ---- epilogue: acc[j] covers rows m0 + 16 warp + lane/4 (+8), cols n0 + 8 j + 2 (lane%4) (+1)
-  const int rbase = m0 + warp * 16 + (lane >> 2);
+  if (ok) {
+    const bool w = tc::mbar_wait_bounded(tc::smem_addr(&mbar[last & 1]), (last >> 1) & 1,
+                                         a.wait_limit);
+    ok = !__syncthreads_or(!w);
+  }
+  tc::fence_after_sync();
+  const int quarter = warp & 3, half = warp >> 2;
+  if (!ok) {
+    if (tid == 0) atomicOr(a.status, 1);
+  } else if (16 * half < N) {
+    uint32_t r[16];
+    tc::tmem_ld16(taddr + ((uint32_t)(quarter * 32) << 16) + 16 * half, r);
+    const int k = k0 + quarter * 32 + lane;
+    if (k < a.kp)
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int m = rbase + 8 * h;
-      if (m >= g.M) continue;
-#pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int n = n0 + 8 * j + 2 * (lane & 3) + e;
-        if (n >= g.n_store) continue;
-        float v = acc[j][2 * h + e];
-        if (EPI == kEpiBiasReluBf16) {
-          v = fmaxf(v + g.bias[n], 0.0f);
-          reinterpret_cast<__nv_bfloat16*>(g.C)[(size_t)m * g.ldc + n] = __float2bfloat16_rn(v);
-        } else if (EPI == kEpiBiasF32) {
-          reinterpret_cast<float*>(g.C)[(size_t)m * g.ldc + n] = v + g.bias[n];
-        } else if (EPI == kEpiF32) {
-          reinterpret_cast<float*>(g.C)[(size_t)m * g.ldc + n] = v;
-        } else {
-          atomicAdd(reinterpret_cast<float*>(g.C) + (size_t)m * g.ldc + n, v);
-        }
+      for (int i = 0; i < 16; ++i) {
+        const int co = 16 * half + i;
+        if (co < a.coutp) atomicAdd(a.dW + (size_t)co * a.kp + k, __uint_as_float(r[i]));
       }
-    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    // after a timeout the MMAs may still be running: give them another bounded wait
+    if (!ok && last >= 0)
+      tc::mbar_wait_bounded(tc::smem_addr(&mbar[last & 1]), (last >> 1) & 1, a.wait_limit);
+    tc::tmem_dealloc(taddr, 32);
   }
 }
 
-template <bool A_ROW, bool B_NK, int EPI>
-void gemm(cudaStream_t s, const GemmArgs& g, int splits) {
-  dim3 grid((g.M + kBM - 1) / kBM, (g.N + kBN - 1) / kBN, splits);
-  k_gemm<A_ROW, B_NK, EPI><<<grid, kGemmThreads, 0, s>>>(g);
+void dcol_tc(cudaStream_t s, const DcolArgs& a) {
+  raise_smem_limit((const void*)k_dcol_tc, dcol_smem_bytes());
+  k_dcol_tc<<<(a.P + kConvM - 1) / kConvM, kBwdThreads, dcol_smem_bytes(), s>>>(a);
 }
 
-// ------------------------------------------------------------------------------ im2col
-// Col[p][k], p = (b, oy, ox), k = (ky * 3 + kx) * Cin + ci for k < 9 Cin, zero up to Kp.
-// Cin = 32: one thread per (p, tap, 8 channels).
-__global__ void k_im2col32(const __nv_bfloat16* __restrict__ X, int B, int H, int W, int Ho,
-                           int Wo, int stride, __nv_bfloat16* __restrict__ col) {
-  const size_t total = (size_t)B * Ho * Wo * 9 * 4;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (size_t)gridDim.x * blockDim.x) {
-    const int q = (int)(t & 3);
-    const size_t pt = t >> 2;
-    const int tap = (int)(pt % 9);
-    const size_t p = pt / 9;
-    const int ox = (int)(p % Wo);
-    const size_t bo = p / Wo;
-    const int oy = (int)(bo % Ho);
-    const int b = (int)(bo / Ho);
-    const int y = oy * stride + tap / 3 - 1, x = ox * stride + tap % 3 - 1;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (y >= 0 && y < H && x >= 0 && x < W)
-      v = *reinterpret_cast<const uint4*>(X + (((size_t)b * H + y) * W + x) * 32 + q * 8);
-    *reinterpret_cast<uint4*>(col + p * 288 + tap * 32 + q * 8) = v;
-  }
-}
-
-// Cin = 2, Kp = 32: one thread per (p, k pair); pair j < 9 is tap j's two channels.
-__global__ void k_im2col2(const __nv_bfloat16* __restrict__ X, int B, int H, int W, int Ho, int Wo,
-                          __nv_bfloat16* __restrict__ col) {
-  const size_t total = (size_t)B * Ho * Wo * 16;
-  for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (size_t)gridDim.x * blockDim.x) {
-    const int j = (int)(t & 15);
-    const size_t p = t >> 4;
-    const int ox = (int)(p % Wo);
-    const size_t bo = p / Wo;
-    const int oy = (int)(bo % Ho);
-    const int b = (int)(bo / Ho);
-    uint32_t v = 0;
-    if (j < 9) {
-      const int y = oy + j / 3 - 1, x = ox + j % 3 - 1;
-      if (y >= 0 && y < H && x >= 0 && x < W)
-        v = *reinterpret_cast<const uint32_t*>(X + (((size_t)b * H + y) * W + x) * 2);
-    }
-    *reinterpret_cast<uint32_t*>(col + p * 32 + 2 * j) = v;
-  }
+// Pixel ranges sized for about two CTAs per SM over all k-tiles.
+template <int N>
+void dw_tc(cudaStream_t s, DwArgs a, int sms) {
+  const int ktiles = (a.kp + 127) / 128;
+  const int ranges = std::max(1, 2 * sms / ktiles);
+  a.chunk = std::max(kDwStage, ((a.P + ranges - 1) / ranges + kDwStage - 1) / kDwStage * kDwStage);
+  raise_smem_limit((const void*)k_dw_tc<N>, dw_smem_bytes(N));
+  dim3 grid((a.P + a.chunk - 1) / a.chunk, ktiles);
+  k_dw_tc<N><<<grid, kBwdThreads, dw_smem_bytes(N), s>>>(a);
 }
 
 // dA(b, y, x, c) = mask(b, y, x, c) * sum over taps with oy = (y + 1 - ky) / s, ox = (x + 1 - kx) / s
@@ -525,6 +724,7 @@ struct pd_cnn {
   float* dW = nullptr;
   float* db = nullptr;
   float* scal = nullptr;     // loss, n_c, n_b
+  int* status = nullptr;     // bit 0: a tensor-core wait of the convolutions ran out
   int step = 0;
   // activations and buffers (sized for max_batch x max_hd x max_wd)
   __nv_bfloat16 *x0 = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr;
@@ -587,47 +787,48 @@ unsigned grid_for(size_t n, int threads) {
   return (unsigned)(b < 152 * 64 ? (b ? b : 1) : 152 * 64);
 }
 
-// Forward pass for B images of Hd x Wd held in net->x0 (or x when given).  Leaves the
-// activations and the im2col buffers of every layer in place for the backward pass.
-void cnn_forward(cudaStream_t s, pd_cnn* net, const __nv_bfloat16* x, int B, const Shapes& sh) {
+// Forward pass for B images of Hd x Wd at x.  With keep_col (training) the patch matrices of every
+// layer are kept, with the activations, for the backward pass.
+void cnn_forward(cudaStream_t s, pd_cnn* net, const __nv_bfloat16* x, int B, const Shapes& sh,
+                 bool keep_col) {
   const NetDesc& d = net->desc;
   const __nv_bfloat16* in[4] = {x, net->a1, net->a2, net->a3};
   __nv_bfloat16* col[4] = {net->col1, net->col2, net->col3, net->col4};
-  __nv_bfloat16* act[3] = {net->a1, net->a2, net->a3};
+  void* act[4] = {net->a1, net->a2, net->a3, net->out};
   for (int l = 0; l < 4; ++l) {
     const LayerDesc& L = d.L[l];
-    const int H = sh.h[l], W = sh.w[l], Ho = sh.h[l + 1], Wo = sh.w[l + 1];
-    const size_t P = (size_t)B * Ho * Wo;
-    if (L.cin == 2)
-      k_im2col2<<<grid_for(P * 16, 256), 256, 0, s>>>(in[l], B, H, W, Ho, Wo, col[l]);
-    else
-      k_im2col32<<<grid_for(P * 36, 256), 256, 0, s>>>(in[l], B, H, W, Ho, Wo, L.stride, col[l]);
-    GemmArgs g{};
-    g.A = col[l];
-    g.B = net->wb + L.wb_off;
-    g.bias = net->bias + 32 * l;
-    g.M = (int)P;
-    g.N = L.coutp;
-    g.K = L.kp;
-    g.lda = L.kp;
-    g.ldb = L.kp;
-    g.k_chunk = L.kp;
-    if (l < 3) {
-      g.C = act[l];
-      g.ldc = 32;
-      g.n_store = 32;
-      gemm<true, true, kEpiBiasReluBf16>(s, g, 1);
+    ConvArgs a{};
+    a.X = in[l];
+    a.B = B;
+    a.H = sh.h[l];
+    a.W = sh.w[l];
+    a.Ho = sh.h[l + 1];
+    a.Wo = sh.w[l + 1];
+    a.stride = L.stride;
+    a.Wt = net->wb + L.wb_off;
+    a.coutp = L.coutp;
+    a.bias = net->bias + 32 * l;
+    a.out = act[l];
+    a.col = keep_col ? col[l] : nullptr;
+    a.status = net->status;
+    a.P = B * a.Ho * a.Wo;
+    a.wait_limit = kConvWaitCycles;
+    a.issue = 1;
+    if (l == 0) {
+      if (keep_col) conv_tc<2, 32, false, true>(s, a);
+      else conv_tc<2, 32, false, false>(s, a);
+    } else if (l < 3) {
+      if (keep_col) conv_tc<32, 32, false, true>(s, a);
+      else conv_tc<32, 32, false, false>(s, a);
     } else {
-      g.C = net->out;
-      g.ldc = 2;
-      g.n_store = 2;
-      gemm<true, true, kEpiBiasF32>(s, g, 1);
+      if (keep_col) conv_tc<32, 16, true, true>(s, a);
+      else conv_tc<32, 16, true, false>(s, a);
     }
   }
 }
 
 // Backward pass from dZ4 (in net->dz4): parameter gradients into net->dW / net->db.
-void cnn_backward(cudaStream_t s, pd_cnn* net, int B, const Shapes& sh) {
+void cnn_backward(cudaStream_t s, pd_cnn* net, int B, const Shapes& sh, int sms) {
   const NetDesc& d = net->desc;
   __nv_bfloat16* dz[4] = {net->dz1, net->dz2, net->dz3, net->dz4};
   __nv_bfloat16* col[4] = {net->col1, net->col2, net->col3, net->col4};
@@ -637,47 +838,38 @@ void cnn_backward(cudaStream_t s, pd_cnn* net, int B, const Shapes& sh) {
   for (int l = 3; l >= 0; --l) {
     const LayerDesc& L = d.L[l];
     const int Ho = sh.h[l + 1], Wo = sh.w[l + 1];
-    const size_t P = (size_t)B * Ho * Wo;
+    const int P = B * Ho * Wo;
     const int ldz = l == 3 ? 8 : 32;
-    // dW[co][k] = sum_p dZ[p][co] Col[p][k]: A = dZ as [K = P][M = coutp], B = Col as [K][N = kp]
-    {
-      GemmArgs g{};
-      g.A = dz[l];
-      g.B = col[l];
-      g.C = net->dW + L.dw_off;
-      g.M = L.coutp;
-      g.N = L.kp;
-      g.K = (int)P;
-      g.lda = ldz;
-      g.ldb = L.kp;
-      g.ldc = L.kp;
-      g.n_store = L.kp;
-      const int chunk = 4096;
-      g.k_chunk = chunk;
-      gemm<false, false, kEpiAtomicF32>(s, g, (int)((P + chunk - 1) / chunk));
-    }
+    // dW[co][k] = sum_p dZ[p][co] Col[p][k]
+    DwArgs w{};
+    w.col = col[l];
+    w.kp = L.kp;
+    w.dZ = dz[l];
+    w.ldz = ldz;
+    w.dW = net->dW + L.dw_off;
+    w.coutp = L.coutp;
+    w.status = net->status;
+    w.P = P;
+    w.wait_limit = kConvWaitCycles;
+    if (l == 3) dw_tc<16>(s, w, sms);
+    else dw_tc<32>(s, w, sms);
     {
       const int threads = 256;
-      const int blocks = (int)std::min<size_t>((P * ldz + 4095) / 4096 + 1, 2048);
+      const int blocks = (int)std::min<size_t>(((size_t)P * ldz + 4095) / 4096 + 1, 2048);
       k_bias_grad<<<blocks, threads, 0, s>>>(dz[l], P, L.cout, ldz, net->db + L.db_off);
     }
     if (l == 0) break;
-    // dCol[p][k] = sum_co dZ[p][co] W[co][k]: A = dZ [M = P][K = coutp], B = W as [K][N = kp]
-    {
-      GemmArgs g{};
-      g.A = dz[l];
-      g.B = net->wb + L.wb_off;
-      g.C = net->dcol;
-      g.M = (int)P;
-      g.N = L.kp;
-      g.K = L.coutp;
-      g.lda = ldz;
-      g.ldb = L.kp;
-      g.ldc = L.kp;
-      g.n_store = L.kp;
-      g.k_chunk = L.coutp;
-      gemm<true, false, kEpiF32>(s, g, 1);
-    }
+    // dCol[p][k] = sum_co dZ[p][co] W[co][k]
+    DcolArgs c{};
+    c.dZ = dz[l];
+    c.ldz = ldz;
+    c.Wt = net->wb + L.wb_off;
+    c.coutp = L.coutp;
+    c.dcol = net->dcol;
+    c.status = net->status;
+    c.P = P;
+    c.wait_limit = kConvWaitCycles;
+    dcol_tc(s, c);
     const int H = sh.h[l], W = sh.w[l];
     const size_t Pin = (size_t)B * H * W;
     k_col2im32<<<grid_for(Pin * 4, 256), 256, 0, s>>>(net->dcol, act_in[l], B, H, W, Ho, Wo,
@@ -713,11 +905,11 @@ pd_status loss_grad_enqueue(pd_ctx* ctx, pd_cnn* net, const __nv_bfloat16* x, co
   cudaStream_t s = ctx->stream;
   const Shapes sh = shapes(Hd, Wd);
   const size_t P4 = (size_t)B * sh.h[4] * sh.w[4];
-  cnn_forward(s, net, x, B, sh);
+  cnn_forward(s, net, x, B, sh, true);
   cudaMemsetAsync(net->scal, 0, 4 * sizeof(float), s);
   k_loss_counts<<<grid_for(P4, 256), 256, 0, s>>>(tgt, P4, net->scal + 1);
   k_loss<<<grid_for(P4, 256), 256, 0, s>>>(net->out, tgt, P4, net->scal + 1, net->dz4, net->scal);
-  cnn_backward(s, net, B, sh);
+  cnn_backward(s, net, B, sh, ctx->sm_count > 0 ? ctx->sm_count : 152);
   return PD_OK;
 }
 
@@ -731,7 +923,7 @@ bool cnn_fits(const pd_cnn* net, int B, int Hd, int Wd) {
 }
 
 const float* cnn_forward_enqueue(cudaStream_t s, pd_cnn* net, const void* x, int Hd, int Wd) {
-  cnn_forward(s, net, reinterpret_cast<const __nv_bfloat16*>(x), 1, shapes(Hd, Wd));
+  cnn_forward(s, net, reinterpret_cast<const __nv_bfloat16*>(x), 1, shapes(Hd, Wd), false);
   return net->out;
 }
 
@@ -793,6 +985,7 @@ pd_status pd_cnn_create(pd_cnn** out, int device, int max_batch, int max_hd, int
   alloc(net->dW, net->dw_elems);
   alloc(net->db, 4 * 32);
   alloc(net->scal, 4);
+  alloc(net->status, 1);
   alloc(net->x0, P[0] * 2);
   alloc(net->a1, P[1] * 32);
   alloc(net->a2, P[2] * 32);
@@ -816,6 +1009,7 @@ pd_status pd_cnn_create(pd_cnn** out, int device, int max_batch, int max_hd, int
          cudaMemset(net->wb, 0, net->wb_elems * sizeof(__nv_bfloat16)) == cudaSuccess &&
          cudaMemset(net->dW, 0, net->dw_elems * sizeof(float)) == cudaSuccess &&
          cudaMemset(net->db, 0, 4 * 32 * sizeof(float)) == cudaSuccess &&
+         cudaMemset(net->status, 0, sizeof(int)) == cudaSuccess &&
          cudaDeviceSynchronize() == cudaSuccess;
   }
   if (!ok) {
@@ -830,7 +1024,7 @@ pd_status pd_cnn_destroy(pd_cnn* net) {
   if (!net) return PD_OK;
   cudaSetDevice(net->device);
   void* ptrs[] = {net->theta, net->adam_m, net->adam_v, net->bias, net->wb, net->dW, net->db,
-                  net->scal, net->x0, net->a1, net->a2, net->a3, net->col1, net->col2, net->col3,
+                  net->scal, net->status, net->x0, net->a1, net->a2, net->a3, net->col1, net->col2, net->col3,
                   net->col4, net->dz1, net->dz2, net->dz3, net->dz4, net->out, net->dcol};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -881,10 +1075,52 @@ pd_status pd_cnn_forward(pd_ctx* ctx, pd_cnn* net, const void* x, int B, int Hd,
   st = cuda_ok(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
   if (st != PD_OK) return st;
   const Shapes sh = shapes(Hd, Wd);
-  cnn_forward(ctx->stream, net, reinterpret_cast<const __nv_bfloat16*>(x), B, sh);
+  cnn_forward(ctx->stream, net, reinterpret_cast<const __nv_bfloat16*>(x), B, sh, false);
   const size_t n = (size_t)B * sh.h[4] * sh.w[4] * 2;
   cudaMemcpyAsync(out, net->out, n * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream);
   return launched(ctx, "pd_cnn_forward");
+}
+
+pd_status pd_cnn_check(pd_ctx* ctx, pd_cnn* net) {
+  if (!ctx) return PD_ERR_INVALID_ARG;
+  if (!net) return fail(ctx, PD_ERR_INVALID_ARG, "network is NULL");
+  pd_status st = cuda_ok(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (st != PD_OK) return st;
+  int flags = 0;
+  st = cuda_ok(ctx, cudaMemcpyAsync(&flags, net->status, sizeof(int), cudaMemcpyDeviceToHost,
+                                    ctx->stream),
+               "status read");
+  if (st != PD_OK) return st;
+  st = cuda_ok(ctx, cudaStreamSynchronize(ctx->stream), "pd_cnn_check");
+  if (st != PD_OK) return st;
+  if (!flags) return PD_OK;
+  cudaMemsetAsync(net->status, 0, sizeof(int), ctx->stream);
+  return fail(ctx, PD_ERR_TIMEOUT, "a tensor-core wait of the band network ran out (flags %d)",
+              flags);
+}
+
+pd_status pd_cnn_probe_timeout(pd_ctx* ctx, pd_cnn* net, long long limit_cycles) {
+  if (!ctx) return PD_ERR_INVALID_ARG;
+  if (!net) return fail(ctx, PD_ERR_INVALID_ARG, "network is NULL");
+  if (limit_cycles < 0 || limit_cycles > kConvWaitCycles)
+    return fail(ctx, PD_ERR_INVALID_ARG, "limit %lld outside [0, %lld]", limit_cycles,
+                kConvWaitCycles);
+  pd_status st = cuda_ok(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (st != PD_OK) return st;
+  // one CTA of the hidden-layer convolution on a 1 x 1 image that issues no MMA
+  ConvArgs a{};
+  a.X = net->a1;
+  a.B = a.H = a.W = a.Ho = a.Wo = a.stride = 1;
+  a.Wt = net->wb + net->desc.L[1].wb_off;
+  a.coutp = 32;
+  a.bias = net->bias + 32;
+  a.out = net->a2;
+  a.status = net->status;
+  a.P = 1;
+  a.wait_limit = limit_cycles;
+  a.issue = 0;
+  conv_tc<32, 32, false, false>(ctx->stream, a);
+  return launched(ctx, "pd_cnn_probe_timeout");
 }
 
 pd_status pd_cnn_loss_grad(pd_ctx* ctx, pd_cnn* net, const void* x, const float* targets, int B,

@@ -70,7 +70,7 @@ def test_forward_matches_oracle(B, ctx, Bn, Hd, Wd):
     net = B.Cnn(0, max_batch=Bn, max_hd=Hd, max_wd=Wd)
     B.pd_cnn_set_params(ctx, net, th)
     out = B.pd_cnn_forward(ctx, net, _to_dev_bf16(x))
-    torch.cuda.synchronize()
+    B.pd_cnn_check(ctx, net)                          # no tensor-core wait ran out
     ref_bf, _ = bc.forward(th, x, store_bf16=True)   # parity: same bf16 layer inputs
     assert out.shape == ref_bf.shape
     assert _rel(out.cpu().numpy(), ref_bf) < 2e-3
@@ -88,7 +88,7 @@ def test_loss_gradient_matches_oracle(B, ctx, Bn, Hd, Wd):
     net = B.Cnn(0, max_batch=Bn, max_hd=Hd, max_wd=Wd)
     B.pd_cnn_set_params(ctx, net, th)
     loss, grad = B.pd_cnn_loss_grad(ctx, net, _to_dev_bf16(x), torch.from_numpy(t).cuda())
-    torch.cuda.synchronize()
+    B.pd_cnn_check(ctx, net)
     g = grad.cpu().numpy()
     # Parity: the oracle on the same bf16-rounded weights and layer inputs (activations and
     # back-propagated gradients stored as bf16, as the GPU stores them): only the accumulation
@@ -105,6 +105,47 @@ def test_loss_gradient_matches_oracle(B, ctx, Bn, Hd, Wd):
     ref_loss, ref_grad = bc.loss_and_grad(th, x, t)
     assert abs(loss.item() - ref_loss) <= 2e-2 * abs(ref_loss)
     assert _rel(g, ref_grad) < 5e-2
+    net.close()
+
+
+def test_forward_is_deterministic_and_batch_independent(B, ctx):
+    """Each image of a batch gives the bits it gives alone (CTAs of 128 output cells straddle
+    image boundaries), and repeated calls give the same bits."""
+    th = _theta(13)
+    x = _input(14, 3, 29, 45)
+    net = B.Cnn(0, max_batch=3, max_hd=29, max_wd=45)
+    B.pd_cnn_set_params(ctx, net, th)
+    xb = _to_dev_bf16(x)
+    whole = B.pd_cnn_forward(ctx, net, xb).clone()
+    again = B.pd_cnn_forward(ctx, net, xb).clone()
+    singles = [B.pd_cnn_forward(ctx, net, xb[i]).clone() for i in range(3)]
+    B.pd_cnn_check(ctx, net)
+    assert torch.equal(whole, again)
+    for i in range(3):
+        assert torch.equal(whole[i], singles[i][0])
+    net.close()
+
+
+def test_tensor_core_wait_timeout_is_reported(B, ctx):
+    """A convolution CTA whose MMAs are never issued gives up its mbarrier wait after the limit,
+    frees its tensor memory and flags the network; the flag is read once and the device stays
+    usable."""
+    net = B.Cnn(0, max_batch=1, max_hd=8, max_wd=8)
+    th = _theta(15)
+    B.pd_cnn_set_params(ctx, net, th)
+    B.pd_cnn_check(ctx, net)
+    B.pd_cnn_probe_timeout(ctx, net, 200000)
+    with pytest.raises(B.PdError) as e:
+        B.pd_cnn_check(ctx, net)
+    assert e.value.status == B.PD_ERR_TIMEOUT
+    B.pd_cnn_check(ctx, net)                          # cleared
+    x = _input(16, 1, 8, 8)
+    out = B.pd_cnn_forward(ctx, net, _to_dev_bf16(x))
+    B.pd_cnn_check(ctx, net)
+    ref_bf, _ = bc.forward(th, x, store_bf16=True)
+    assert _rel(out.cpu().numpy(), ref_bf) < 2e-3
+    with pytest.raises(B.PdError):
+        B.pd_cnn_probe_timeout(ctx, net, -1)
     net.close()
 
 
