@@ -408,6 +408,20 @@ def bench_band(B, torch, synth, steps=10, n_eval=4):
         band_only_ms = timed(lambda: B.pd_sgm_band(ctx, left, right, model, p, tl, 17, kap, d_int,
                                                    D1))
         net.close()
+        # one Adam step of the network at its training configuration (16 pairs' inputs per step)
+        Hd, Wd, Bt = (H + 3) // 4, (W + 3) // 4, 16
+        tnet = B.Cnn(torch.cuda.current_device(), Bt, Hd, Wd)
+        B.pd_cnn_set_params(ctx, tnet, band.load_params())
+        gen = torch.Generator(device="cuda").manual_seed(7)
+        xt = torch.randn((Bt, Hd, Wd, 2), generator=gen, device="cuda").to(torch.bfloat16)
+        Ho, Wo = (Hd + 3) // 4, (Wd + 3) // 4
+        tt = torch.zeros((Bt, Ho, Wo, 4), dtype=torch.float32, device="cuda")
+        tt[..., 0] = torch.randint(0, D, (Bt, Ho, Wo), generator=gen, device="cuda").float()
+        tt[..., 2:] = 1.0
+        lt = torch.zeros(1, dtype=torch.float32, device="cuda")
+        train_ms = timed(lambda: B.pd_cnn_train_step(ctx, tnet, xt, tt, 1e-4, lt))
+        B.pd_cnn_check(ctx, tnet)
+        tnet.close()
         ctx.close()
     disp = W * H * D
     return {"workload": "road_1920x1080_d128_8paths, learned 17-disparity band per 16x16 tile "
@@ -416,6 +430,7 @@ def bench_band(B, torch, synth, steps=10, n_eval=4):
             "learned_Mdisp_s": disp / (learned_ms * 1e-3) / 1e6,
             "full_range_Mdisp_s": disp / (full_ms * 1e-3) / 1e6,
             "cnn_ms": cnn_ms, "band_sgm_ms": band_only_ms,
+            "cnn_train_step_ms": train_ms, "cnn_train_batch": "16 x 270 x 480 cells",
             "banded_tile_fraction": statistics.mean(frac),
             "disagreement_mean": statistics.mean(dis), "disagreement_max": max(dis),
             "constant_centre_disagreement_mean": statistics.mean(const_dis)}

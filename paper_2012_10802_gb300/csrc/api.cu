@@ -225,19 +225,24 @@ pd_status sgm_enqueue(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, in
 }
 
 // Enqueues the band-restricted SGM (no validation; scratch already sized).
+// census_done: the row shifts and the census codes (sc.kappa or kappa, sc.cl, sc.cr) are already
+// enqueued ahead of this call on ctx's stream.
 pd_status sgm_band_enqueue(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, int W, int H,
                            size_t pitch, const pd_road_model* model, const pd_params* p,
                            const BandArgs& band, int32_t* kappa, int16_t* d_int, float* D1,
-                           pd_prof_rec* rec) {
+                           pd_prof_rec* rec, bool census_done = false) {
   cudaStream_t s = ctx->stream;
   SgmScratch sc = sgm_carve(ctx->ws, W, H, p->D, p->paths);
   int32_t* kap = kappa ? kappa : sc.kappa;
   size_t N = (size_t)W * H;
   size_t vol = N * p->D;
   mark(ctx, rec, 0);
-  launch_kappa(s, W, H, model->order, model->a, cos(model->roll), sin(model->roll),
-               (double)p->delta_pt, kap);
-  launch_census_pair(s, left, right, W, H, pitch, kap, sc.cl, sc.cr);
+  if (!census_done) {
+    launch_kappa(s, W, H, model->order, model->a, cos(model->roll), sin(model->roll),
+                 (double)p->delta_pt, kap);
+    launch_census_pair(s, left, right, W, H, pitch, kap, sc.cl, sc.cr);
+    count_launches(ctx, 2);
+  }
   launch_cost_band(s, sc.cl, sc.cr, W, H, p->D, band, sc.cost);
   cudaMemsetAsync(sc.rkeys, 0xff, N * sizeof(uint32_t), s);
   mark(ctx, rec, 1);
@@ -247,7 +252,7 @@ pd_status sgm_band_enqueue(pd_ctx* ctx, const uint8_t* left, const uint8_t* righ
   launch_wta_band(s, sc.vols, p->paths, vol, W, H, p->D, band, d_int, sc.dsub, sc.rkeys);
   launch_lr_band(s, d_int, sc.dsub, sc.rkeys, kap, W, H, p->D, band, p->lr_tol, D1);
   mark(ctx, rec, 3);
-  count_launches(ctx, 6);
+  count_launches(ctx, 4);
   return launched(ctx, "pd_sgm_band");
 }
 
@@ -600,6 +605,9 @@ pd_status pd_destroy(pd_ctx* ctx) {
   for (auto& e : ctx->cap_ev)
     if (e) cudaEventDestroy(e);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   delete static_cast<std::vector<long long>*>(ctx->graph_sig);
   delete static_cast<std::map<std::vector<long long>, int>*>(ctx->tuned);
@@ -801,15 +809,30 @@ pd_status pd_sgm_learned(pd_ctx* ctx, pd_cnn* net, const uint8_t* left, const ui
   SgmScratch sc = sgm_carve(ctx->ws, W, H, params->D, params->paths);
   int32_t* kap = kappa ? kappa : sc.kappa;
   cudaStream_t s = ctx->stream;
+  if (!ctx->side) {
+    PD_TRY(cuda_ok(ctx, cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking),
+                   "side stream"));
+    PD_TRY(cuda_ok(ctx, cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming),
+                   "fork event"));
+    PD_TRY(cuda_ok(ctx, cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming),
+                   "join event"));
+  }
+  pd_prof_rec* rec = prof_begin(ctx);
   launch_kappa(s, W, H, model->order, model->a, cos(model->roll), sin(model->roll),
                (double)params->delta_pt, kap);
+  // the census needs only the row shifts: it runs on the side stream beside the network
+  cudaEventRecord(ctx->fork_ev, s);
+  cudaStreamWaitEvent(ctx->side, ctx->fork_ev, 0);
+  launch_census_pair(ctx->side, left, right, W, H, pitch, kap, sc.cl, sc.cr);
+  cudaEventRecord(ctx->join_ev, ctx->side);
   launch_band_input(s, left, right, W, H, pitch, kap, x);
   const float* out = cnn_forward_enqueue(s, net, x, Hd, Wd);
   launch_band_tiles(s, out, th, tw, params->D, band_width, tl);
-  count_launches(ctx, 11);
+  cudaStreamWaitEvent(s, ctx->join_ev, 0);
+  count_launches(ctx, 8);  // row shifts, census, network input, four convolutions, windows
   BandArgs band{tl, tw, band_width};
-  return sgm_band_enqueue(ctx, left, right, W, H, pitch, model, params, band, kap, d_int, D1,
-                          prof_begin(ctx));
+  return sgm_band_enqueue(ctx, left, right, W, H, pitch, model, params, band, kap, d_int, D1, rec,
+                          true);
 }
 
 pd_status pd_transform_robust(pd_ctx* ctx, const float* D1, int W, int H, int order,

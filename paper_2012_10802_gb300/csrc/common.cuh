@@ -48,6 +48,9 @@ struct pd_ctx {
   cudaEvent_t cap_ev[7] = {};         // events of the captured stage marks
   cudaGraphNode_t cap_node[7] = {};
   int cap_used = 0;
+  // second stream of the learned band path (the census runs beside the network)
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
 };
 
 namespace pd {
