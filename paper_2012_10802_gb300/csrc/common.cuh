@@ -55,6 +55,15 @@ struct pd_ctx {
 
 namespace pd {
 
+// rint(x) (ties to even) as a 64-bit integer, equal to __float2ll_rn(x).  For |x| < 2^22 one
+// float add puts rint(x) into the low mantissa bits of x + 1.5 * 2^23, whose unit in the last
+// place is 1; larger or non-finite x take the 64-bit conversion instruction, which issues at the
+// FP64 rate on this GPU.
+__device__ __forceinline__ long long rint_to_ll(float x) {
+  if (fabsf(x) < 4194304.0f) return (long long)(__float_as_int(x + 12582912.0f) - 0x4B400000);
+  return __float2ll_rn(x);
+}
+
 constexpr int kCensusBits = 24;
 constexpr int kMaxD = 256;
 constexpr int kMaxImage = 4096;  // W, H limit of the exact moment sums

@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(kTileThreads) k_slic_assign(
     }
 #pragma unroll
     for (int h = 0; h < NP; ++h) {
-      if (inside[h]) q[h] = __float2ll_rn(val[h] * 1024.0f);  // exact scaling; rint's rounding
+      if (inside[h]) q[h] = rint_to_ll(val[h] * 1024.0f);  // exact scaling; rint's rounding
       // a label's slot is the same for every lane that has it, so grouping by label groups by
       // slot; lanes that kept an uncovered pixel's old label (slot -1) go straight to the global
       // sums
@@ -332,8 +332,9 @@ __global__ void k_centres_out(int n, const float* __restrict__ cx, const float* 
 // ------------------------------------------------------------------- Eqs. (14)-(17)
 constexpr int kBins = 257;  // k = 0..255 plus an overflow bin for everything at or above 32 px
 
-// Adds (1, a, b, a^2 + b^2) of the lanes sharing a bin into the shared histogram h, one lane per
-// distinct bin.  All 32 lanes must call it.  The sums use the single-instruction warp reduction on
+// Adds (1, a, b, a^2 + b^2) of the lanes sharing a bin into the shared histogram h, one pass per
+// distinct bin of the warp, lanes 0-3 adding the bin's four sums in one atomic instruction.  All
+// 32 lanes must call it.  The sums use the single-instruction warp reduction on
 // 32-bit values; a and b (D2 below 2^16 px) fit, a^2 + b^2 is split into 16/16/32-bit parts.
 __device__ void warp_hist(bool valid, int bin, long long a, long long b,
                           unsigned long long (*h)[4]) {
@@ -350,13 +351,14 @@ __device__ void warp_hist(bool valid, int bin, long long a, long long b,
     const unsigned s0 = __reduce_add_sync(0xffffffffu, mine ? (unsigned)(sq & 0xffffu) : 0u);
     const unsigned s1 = __reduce_add_sync(0xffffffffu, mine ? (unsigned)((sq >> 16) & 0xffffu) : 0u);
     const unsigned s2 = __reduce_add_sync(0xffffffffu, mine ? (unsigned)(sq >> 32) : 0u);
-    if (lane == leader) {
+    if (lane < 4) {  // the four sums of the bin, one lane each, in one atomic instruction
       const unsigned long long ssq = (unsigned long long)s0 + ((unsigned long long)s1 << 16) +
                                      ((unsigned long long)s2 << 32);
-      atomicAdd(&h[bl][0], (unsigned long long)__popc(peers));
-      atomicAdd(&h[bl][1], (unsigned long long)(long long)sa);
-      atomicAdd(&h[bl][2], (unsigned long long)(long long)sb);
-      atomicAdd(&h[bl][3], ssq);
+      const unsigned long long val = lane == 0   ? (unsigned long long)__popc(peers)
+                                     : lane == 1 ? (unsigned long long)(long long)sa
+                                     : lane == 2 ? (unsigned long long)(long long)sb
+                                                 : ssq;
+      atomicAdd(&h[bl][lane], val);
     }
     pending &= ~peers;
   }
@@ -381,7 +383,7 @@ __global__ void __launch_bounds__(256) k_thresh_hist(const float* __restrict__ D
         for (int dx = -1; dx <= 1; ++dx) {
           size_t q = (size_t)(v + dy) * W + (u + dx);
           if (!(D1[q] >= 0.0f)) ok = false;
-          long long qq = __float2ll_rn(D2[q] * 1024.0f);
+          long long qq = rint_to_ll(D2[q] * 1024.0f);
           if (dx == 0 && dy == 0)
             a = qq;
           else

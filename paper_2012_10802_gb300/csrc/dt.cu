@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(kMomThreads) k_moments_partial(const float* __
     const int pi = (int)p;  // W * H <= 2^24: a 32-bit division
     int u = pi % W, v = pi / W;
     if (fit && !(fabsf(d - road_f32(cf, u, v)) <= tau)) continue;
-    long long q = __float2ll_rn(d * 1024.0f);  // exact scaling; rounds half to even like rint
+    long long q = rint_to_ll(d * 1024.0f);  // exact scaling; rounds half to even like rint
     long long ut = 2LL * u - (W - 1), vt = 2LL * v - (H - 1);
     long long up[5], vp[5];
     up[0] = vp[0] = 1;

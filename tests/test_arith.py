@@ -5,6 +5,8 @@
   53 >= 2 x 24 + 2), also after the exact scaling by 1/1024.
 * Mask comparison (Eq. 17): for a float x and a double t, x < t exactly when x < t rounded up to
   a float.
+* Fixed-point values rint(1024 D) (Secs. II-C, II-D, II-E): for float |x| < 2^22, rint(x) is the
+  low mantissa field of the float sum x + 1.5 * 2^23.
 """
 import numpy as np
 
@@ -43,3 +45,28 @@ def test_float_compare_against_threshold_rounded_up():
                        tf, np.nextafter(tf, np.float32(-np.inf)), np.float32(-np.inf),
                        np.float32(np.inf), np.float32(np.nan)], np.float32)
         assert np.array_equal(np.float64(xs) < t, xs < tf)
+
+
+def _rint_by_add(x):
+    """rint of float32 values |x| < 2^22 through one float add of 1.5 * 2^23: the sum's unit in the
+    last place is 1, so its low mantissa bits hold rint(x) (ties to even)."""
+    s = (np.asarray(x, np.float32) + np.float32(12582912.0)).astype(np.float32)
+    return s.view(np.int32).astype(np.int64) - 0x4B400000
+
+
+def test_rint_by_float_add_matches_rint():
+    rng = np.random.default_rng(5)
+    lim = 1 << 22
+    x = np.concatenate([
+        rng.uniform(-lim, lim, 300000),
+        rng.normal(0, 300, 100000),                                    # disparity-like values
+        np.arange(-2000, 2000) + 0.5,                                  # ties
+        np.arange(-2000, 2000) * 1024.0 + 512.0,                       # ties of 1024 x
+        [0.0, -0.0, 0.5, -0.5, 1.5, -1.5, 2.5, lim - 0.5, -(lim - 0.5), lim - 1, -(lim - 1)],
+    ]).astype(np.float32)
+    x = x[np.abs(x) < lim]
+    assert np.array_equal(_rint_by_add(x), np.rint(x.astype(np.float64)).astype(np.int64))
+    # the scaled inputs of the kernels: rint(1024 * v) for float v, 1024 v exact
+    v = rng.normal(0, 40, 200000).astype(np.float32)
+    xv = (v * np.float32(1024.0)).astype(np.float32)
+    assert np.array_equal(_rint_by_add(xv), np.rint(v.astype(np.float64) * 1024.0).astype(np.int64))
