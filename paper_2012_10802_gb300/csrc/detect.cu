@@ -408,6 +408,7 @@ __global__ void __launch_bounds__(256) k_thresh_hist(const float* __restrict__ D
 // (region 1: kmax bins below k, region 2: kmin bins from k up), evaluates E2 in double, and the
 // block takes the smallest minimising k; t_s from mode.
 constexpr int kSolveThreads = 256;
+static_assert(kSolveThreads == kBins - 1, "one solve thread per bin below the overflow bin");
 
 // Inclusive block scan (sum) of one 64-bit value per thread; 256 threads.
 __device__ long long block_scan_ll(long long v, long long* tmp) {
@@ -436,20 +437,18 @@ __global__ void __launch_bounds__(kSolveThreads) k_thresh_solve(
   const unsigned long long(*hmin)[4] = reinterpret_cast<const unsigned long long(*)[4]>(hist + kBins * 4);
   // region 1 at threshold k: kmax bins 0..k-1 (exclusive prefix sums of bins 0..255);
   // region 2 at threshold k: kmin bins k..256 (total minus the exclusive prefix)
+  // totals of the kmin histogram over all 257 bins: the last thread's inclusive prefix (bins
+  // 0..255) plus the overflow bin
+  __shared__ long long tot[4];
   long long r1[4], r2[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     long long xm = (long long)hmax[k][q];
     r1[q] = block_scan_ll(xm, tmp) - xm;
     long long xn = (long long)hmin[k][q];
-    r2[q] = block_scan_ll(xn, tmp) - xn;  // exclusive prefix of kmin bins below k
-  }
-  // totals of the kmin histogram over all 257 bins
-  __shared__ long long tot[4];
-  if (k < 4) {
-    long long t = 0;
-    for (int j = 0; j < kBins; ++j) t += (long long)hmin[j][k];
-    tot[k] = t;
+    const long long incl = block_scan_ll(xn, tmp);
+    r2[q] = incl - xn;  // exclusive prefix of kmin bins below k
+    if (k == kSolveThreads - 1) tot[q] = incl + (long long)hmin[kBins - 1][q];
   }
   __syncthreads();
   double e = NAN;
