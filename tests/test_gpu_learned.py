@@ -63,3 +63,33 @@ def test_learned_band_on_the_numpy_rendered_pair(B, setup):
     tl, _, d, D1 = B.pd_sgm_learned(ctx, net, left, right, model, p, 17)
     torch.cuda.synchronize()
     assert band.disagreement(d, D1, d_full, D1_full, D) <= 0.005
+
+
+def test_learned_path_profiled_and_on_a_user_stream(B, setup):
+    """The learned path forks its census onto a second stream of the context and joins it before
+    the banded cost: profiled calls and calls on a caller's stream give the same bits as a plain
+    call, and count their launches (row shifts, census, network input, four convolutions, windows,
+    then the banded cost, aggregation, winner and check)."""
+    band, ctx, net = setup
+    sc = synth.road_scaled(W, H, band.TEST_SEED0 + 1)
+    left, right = synth.render_torch(sc, "cuda")
+    model = B.RoadModel.make(*synth.true_model(sc))
+    p = B.default_params(D=D)
+    ref = [t.clone() for t in B.pd_sgm_learned(ctx, net, left, right, model, p, 17)]
+    torch.cuda.synchronize()
+    B.pd_profile_enable(ctx, True)
+    got = B.pd_sgm_learned(ctx, net, left, right, model, p, 17)
+    prof = B.pd_profile_read(ctx)
+    B.pd_profile_enable(ctx, False)
+    for a, b in zip(ref, got):
+        assert torch.equal(a, b)
+    assert prof["calls"] == 1 and prof["launches"] == 12
+    assert prof["aggregate_ms"] > 0.0 and prof["disparity_ms"] > 0.0
+    user = torch.cuda.Stream()
+    c2 = B.Context(0, stream=user)
+    with torch.cuda.stream(user):
+        got2 = B.pd_sgm_learned(c2, net, left, right, model, p, 17)
+    user.synchronize()
+    for a, b in zip(ref, got2):
+        assert torch.equal(a, b)
+    c2.close()
