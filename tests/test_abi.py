@@ -63,3 +63,17 @@ def test_create_without_gpu_fails_cleanly(libpath):
     h = ctypes.c_void_p()
     assert binding.lib().pd_create(ctypes.byref(h), 0, None) == binding.PD_ERR_INVALID_ARG
     assert binding.lib().pd_destroy(None) == binding.PD_OK
+
+
+def test_null_handles_are_rejected_without_a_launch(libpath):
+    """Calls that take a context or a network reject NULL handles before touching a device."""
+    from paper_2012_10802_gb300 import binding
+    L = binding.lib()
+    assert L.pd_cnn_check(None, None) == binding.PD_ERR_INVALID_ARG
+    assert L.pd_cnn_probe_timeout(None, None, 1000) == binding.PD_ERR_INVALID_ARG
+    assert L.pd_pipeline_config(None, 1) == binding.PD_ERR_INVALID_ARG
+    assert L.pd_cnn_destroy(None) == binding.PD_OK
+    h = ctypes.c_void_p()
+    assert L.pd_cnn_create(ctypes.byref(h), 0, 0, 8, 8) == binding.PD_ERR_INVALID_ARG  # batch 0
+    assert L.pd_cnn_create(None, 0, 1, 8, 8) == binding.PD_ERR_INVALID_ARG
+    assert binding.pd_cnn_num_params() == 19682
