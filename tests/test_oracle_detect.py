@@ -33,6 +33,123 @@ def test_slic_first_iteration_on_constant_map_is_voronoi(orc):
     assert np.array_equal(labels, np.argmin(d2, axis=2))
 
 
+def _bowls(W, H, nx, ny, targets):
+    """A D2 map made of one quadratic bowl per grid cell, a (x - x0)^2 + b (y - y0)^2 with the
+    bowl's centre (x0, y0) at `targets[k]` for cell k.  The central-difference gradient of Sec.
+    II-D is then 16 a^2 (x - x0)^2 + 16 b^2 (y - y0)^2 inside the cell: zero at the bowl's centre
+    when that is a pixel, and equal on the two pixels around a half-integer centre.  With
+    a = b = 1/4 and half-integer centres every value is exact in float32."""
+    D2 = np.zeros((H, W), np.float32)
+    v, u = np.mgrid[0:H, 0:W]
+    cell = (v * ny // H) * nx + (u * nx // W)
+    for k, (x0, y0) in enumerate(targets):
+        sel = cell == k
+        D2[sel] = (0.25 * (u[sel] - x0) ** 2 + 0.25 * (v[sel] - y0) ** 2 + 4.0).astype(np.float32)
+    return D2
+
+
+def test_slic_seed_moves_to_the_unique_gradient_minimum(orc):
+    """Sec. II-D moves each grid seed to the lowest-gradient pixel of its 3x3 neighbourhood.  A
+    30x30 map with K = 9 has seeds at (5 + 10 i, 5 + 10 j); each cell holds a bowl whose unique
+    gradient minimum is one of the nine offsets of its seed, so with zero iterations the returned
+    centres are exactly the moved seeds (and their D2 values).  A seed that moved to the largest
+    gradient, a one-sided difference or a swapped offset fails."""
+    W = H = 30
+    n, nx, ny = orc.slic_grid(W, H, 9)
+    assert (n, nx, ny) == (9, 3, 3)
+    offs = [(-1, -1), (0, -1), (1, -1), (-1, 0), (0, 0), (1, 0), (-1, 1), (0, 1), (1, 1)]
+    seeds = [(5 + 10 * i, 5 + 10 * j) for j in range(3) for i in range(3)]
+    targets = [(sx + ox, sy + oy) for (sx, sy), (ox, oy) in zip(seeds, offs)]
+    D2 = _bowls(W, H, nx, ny, targets)
+    _, centres = orc.slic(D2, 9, 10.0, 0)
+    for k, (tx, ty) in enumerate(targets):
+        assert (centres[k, 0], centres[k, 1]) == (tx, ty), k
+        assert centres[k, 2] == D2[ty, tx]
+
+
+def test_slic_seed_move_ties(orc):
+    """Ties of the seed move: the seed itself wins a tie with any neighbour, even one that comes
+    earlier in raster order; between two neighbours the first in raster order (row, then column)
+    wins.  Bowl centres on half-integers make the two pixels around them equal minima."""
+    W = H = 30
+    _, nx, ny = orc.slic_grid(W, H, 9)
+    seeds = [(5 + 10 * i, 5 + 10 * j) for j in range(3) for i in range(3)]
+    cases = [
+        ((-0.5, 0.0), (0, 0)),    # seed ties its left neighbour: the seed stays
+        ((0.5, 0.0), (0, 0)),     # seed ties its right neighbour: the seed stays
+        ((0.0, -0.5), (0, 0)),    # seed ties the pixel above it: the seed stays
+        ((0.5, 1.0), (0, 1)),     # (0, 1) and (1, 1) tie: raster order takes (0, 1)
+        ((-0.5, -1.0), (-1, -1)),  # (-1, -1) and (0, -1) tie: (-1, -1) comes first
+        ((1.0, -0.5), (1, -1)),   # (1, -1) and (1, 0) tie: the upper row comes first
+        ((-1.0, 0.5), (-1, 0)),   # (-1, 0) and (-1, 1) tie
+        ((0.0, 0.0), (0, 0)),     # plain minimum at the seed
+        ((1.0, 1.0), (1, 1)),     # plain minimum at a corner
+    ]
+    targets = [(sx + c[0][0], sy + c[0][1]) for (sx, sy), c in zip(seeds, cases)]
+    D2 = _bowls(W, H, nx, ny, targets)
+    _, centres = orc.slic(D2, 9, 10.0, 0)
+    for k, ((sx, sy), (_, (ex, ey))) in enumerate(zip(seeds, cases)):
+        assert (centres[k, 0], centres[k, 1]) == (sx + ex, sy + ey), k
+
+
+def _assign(D2, cx, cy, cv, S, coef, prev):
+    """One assignment of Sec. II-D over every centre with the distance in float32, in the
+    order dv^2 + (dx^2 + dy^2) coef, the lower index on ties, uncovered pixels unchanged."""
+    H, W = D2.shape
+    v, u = np.mgrid[0:H, 0:W]
+    best = np.full((H, W), np.inf, np.float32)
+    lab = prev.copy()
+    for k in range(len(cx)):
+        fx = (u.astype(np.float32) - cx[k]).astype(np.float32)
+        fy = (v.astype(np.float32) - cy[k]).astype(np.float32)
+        win = (np.abs(fx) <= S) & (np.abs(fy) <= S)
+        dv = (D2 - cv[k]).astype(np.float32)
+        dd = dv * dv + (fx * fx + fy * fy) * coef
+        take = win & (dd < best)
+        best[take] = dd[take]
+        lab[take] = k
+    return lab
+
+
+def _means(D2, labels, n, old):
+    """Centre update of Sec. II-D in Python integers: the mean of x, y and rint(1024 D2) over
+    the members (one double division each, then float32); empty clusters keep their centre."""
+    H, W = D2.shape
+    q = np.rint(D2.astype(np.float64) * 1024).astype(np.int64)
+    out = old.copy()
+    for k in range(n):
+        ys, xs = np.nonzero(labels == k)
+        c = len(xs)
+        if c == 0:
+            continue
+        out[k, 0] = np.float32(int(xs.sum()) / c)
+        out[k, 1] = np.float32(int(ys.sum()) / c)
+        out[k, 2] = np.float32((int(q[ys, xs].sum()) / c) / 1024.0)
+    return out
+
+
+def test_slic_centre_update_and_second_assignment(orc):
+    """The centre update of Sec. II-D, recomputed in Python integers from the oracle's first
+    assignment, equals the oracle's centres after one iteration bit for bit; the second
+    assignment against those centres gives the oracle's two-iteration labels, whose means are
+    its two-iteration centres.  A mean over the wrong coordinate, a dropped 1024 scale or an
+    update that skips the pixels' values fails."""
+    rng = np.random.default_rng(11)
+    H, W, K, m = 48, 64, 12, 10.0
+    D2 = (16 + rng.normal(0, 1.5, (H, W))).astype(np.float32)
+    D2[20:38, 10:40] -= 6.0
+    n, _, _ = orc.slic_grid(W, H, K)
+    _, c0 = orc.slic(D2, K, m, 0)
+    l1, c1 = orc.slic(D2, K, m, 1)
+    assert np.array_equal(_means(D2, l1, n, c0), c1)
+    S = np.float32(np.sqrt(W * H / K))
+    coef = np.float32(m * m * K / (W * H))
+    l2, c2 = orc.slic(D2, K, m, 2)
+    assert np.array_equal(_assign(D2, c1[:, 0], c1[:, 1], c1[:, 2], S, coef, l1), l2)
+    assert np.array_equal(_means(D2, l2, n, c1), c2)
+    assert not np.array_equal(l1, l2)  # the second round changes labels: it is exercised
+
+
 def test_slic_boundaries_follow_a_deep_step(orc):
     """A pit 20 px deep in a flat map: after the iterations no superpixel straddles its edge."""
     H, W = 120, 160
