@@ -29,6 +29,11 @@ def ctx(B):
     c.close()
 
 
+# Per-layer bound on the relative gradient gap to the exact float64 network (layers 0..3).  The
+# bf16-storage oracle measures at most 5.2 %, 4.6 %, 3.5 % and 0.2 % on the shapes below.
+FP64_LAYER_BOUND = (8e-2, 7e-2, 5e-2, 5e-3)
+
+
 def _rel(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-30))
 
@@ -101,10 +106,23 @@ def test_loss_gradient_matches_oracle(B, ctx, Bn, Hd, Wd):
         for sl in (slice(k, k + nw), slice(k + nw, k + nw + co)):
             assert _rel(g[sl], bf_grad[sl]) < 2e-3, (li, _rel(g[sl], bf_grad[sl]))
         k += nw + co
-    # Against the exact float64 network the bf16 storage costs a few percent at most.
+    # Against the exact float64 network, layer by layer.  Storing activations and
+    # back-propagated gradients as bf16 costs the first layers a few percent (they sit at the end
+    # of the longest chain of bf16 roundings); the bounds below are per layer, weights then bias.
+    # The GPU's gap must also equal the bf16-storage oracle's own gap to within 1e-3: the bf16
+    # storage, not the kernels, is then the whole difference from the exact network.
     ref_loss, ref_grad = bc.loss_and_grad(th, x, t)
     assert abs(loss.item() - ref_loss) <= 2e-2 * abs(ref_loss)
-    assert _rel(g, ref_grad) < 5e-2
+    k = 0
+    for li, (ci, co, _, _) in enumerate(bc.LAYERS):
+        nw = co * 9 * ci
+        for part, sl in (("w", slice(k, k + nw)), ("b", slice(k + nw, k + nw + co))):
+            gap = _rel(g[sl], ref_grad[sl])
+            own = _rel(bf_grad[sl], ref_grad[sl])
+            print(f"layer {li} {part}: gap to float64 {gap:.4f} (bf16-storage oracle {own:.4f})")
+            assert gap < FP64_LAYER_BOUND[li], (li, part, gap)
+            assert abs(gap - own) < 1e-3, (li, part, gap, own)
+        k += nw + co
     net.close()
 
 
