@@ -240,7 +240,9 @@ pd_status pd_transform(pd_ctx* ctx, const float* D1, int W, int H, int order, fl
  *    PD_ERR_INVALID_ARG without launching anything.  So do NULL D1/D2, an order other than 1 or 2
  *    and a non-finite delta_dt.  Launch failures return PD_ERR_CUDA.
  *  - The first call on a device looks up the array's device address on that device (the current
- *    one); make that first call before any stream capture.
+ *    one); make that first call before any stream capture.  After a device reset
+ *    (cudaDeviceReset) the next call on that device looks the address up again, so make it
+ *    outside a capture too.
  *  - All calls share the one array: calls that may overlap on the GPU (different streams, or
  *    different host threads on one device) race and must be serialised by the caller.  Each call
  *    overwrites what the previous one left there before reading it. */
@@ -281,6 +283,17 @@ pd_status pd_profile_enable(pd_ctx* ctx, int on);
 /* Waits for the recorded events, writes the summed stage times to *out (host) and starts a new
  * recording. */
 pd_status pd_profile_read(pd_ctx* ctx, pd_profile* out);
+
+/* Measured integer peak for the roofline of Eq. (8) (a measurement aid; the paper has no
+ * counterpart).  Runs a kernel of independent packed u16x2 DPX instructions (three-input minimum
+ * and fused add-minimum, the instructions of the aggregation's recurrence) at 64 warps per SM,
+ * `reps` rounds of 16 instructions per thread (reps in [1, 2^20]; 4096 takes about 1 ms), once
+ * to warm up and once timed with CUDA events on the context's stream; synchronises the stream.
+ * lane_ops_per_s (host, may be NULL): u16 lane-operations per second (2 per thread instruction);
+ * instr_per_clk_sm (host, may be NULL): thread instructions per SM clock, averaged over the SMs
+ * from each SM's own clock counter, so independent of the clock it ran at.  Uses the context's
+ * scratch. */
+pd_status pd_int_rate(pd_ctx* ctx, int reps, double* lane_ops_per_s, double* instr_per_clk_sm);
 
 /* ------------------------------------------------- batched form (an extension of the paper) */
 

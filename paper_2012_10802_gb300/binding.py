@@ -127,6 +127,7 @@ SIGNATURES = {
     "pd_profile_enable": [_P, _i],
     "pd_pipeline_config": [_P, _i],
     "pd_profile_read": [_P, C.POINTER(Profile)],
+    "pd_int_rate": [_P, _i, C.POINTER(C.c_double), C.POINTER(C.c_double)],
 }
 EXTRA = {"pd_last_error": (C.c_char_p, [_P]), "pd_workspace_bytes": (C.c_size_t, [_P]),
          "pd_cnn_num_params": (C.c_int, [])}
@@ -598,13 +599,22 @@ def pd_profile_read(ctx):
     return p.as_dict()
 
 
+def pd_int_rate(ctx, reps=4096):
+    """Measured packed u16x2 DPX issue rate: (u16 lane-ops per second, thread instructions per
+    SM clock)."""
+    a, b = C.c_double(), C.c_double()
+    ctx.check(lib().pd_int_rate(ctx.h, int(reps), C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
 def pd_transform_noalloc(D1, order, delta_dt, fitted, D2, stream=None):
     """The allocation-free transform: no context, fixed library scratch; outputs must be given."""
     H, W = D1.shape
     if stream is None:
         stream = torch.cuda.current_stream(D1.device)
-    return lib().pd_transform_noalloc(_ptr(D1), W, H, order, float(delta_dt), _ptr(fitted),
-                                      _ptr(D2), C.c_void_p(stream.cuda_stream))
+    with torch.cuda.device(D1.device):     # the C side works on the current device
+        return lib().pd_transform_noalloc(_ptr(D1), W, H, order, float(delta_dt), _ptr(fitted),
+                                          _ptr(D2), C.c_void_p(stream.cuda_stream))
 
 
 def pd_batch_config(ctx, scratch_budget_bytes=0, use_graph=False, autotune=True):

@@ -550,7 +550,42 @@ namespace pd {
 namespace {
 constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mu;
+// Per device: the unique id of the context the address was looked up in, and the address.  A
+// device reset (cudaDeviceReset) destroys the context and unloads the module, so the address is
+// looked up again whenever the current context's id differs from the cached one.
+unsigned long long g_noalloc_ctx[kNoAllocMaxDevices] = {0};
 void* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+
+// cuCtxGetCurrent and cuCtxGetId, reached through the runtime's driver entry points so that the
+// library does not link the driver library itself.
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+// The unique id of the calling thread's current context, or 0 if it cannot be had.  Called with
+// g_noalloc_mu held.
+unsigned long long current_context_id() {
+  if (!g_ctx_get_current || !g_ctx_get_id) {
+    void* a = nullptr;
+    void* b = nullptr;
+    cudaDriverEntryPointQueryResult qa, qb;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) !=
+            cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) !=
+            cudaSuccess ||
+        qa != cudaDriverEntryPointSuccess || qb != cudaDriverEntryPointSuccess || !a || !b) {
+      cudaGetLastError();
+      return 0;
+    }
+    g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(a);
+    g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(b);
+  }
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (g_ctx_get_current(&ctx) != 0 || !ctx || g_ctx_get_id(ctx, &id) != 0) return 0;
+  return id;
+}
 }  // namespace
 
 }  // namespace pd
@@ -573,17 +608,21 @@ extern "C" pd_status pd_transform_noalloc(const float* D1, int W, int H, int ord
   if (dev < 0 || dev >= kNoAllocMaxDevices) return PD_ERR_UNSUPPORTED;
   void* base = nullptr;
   {
-    // one-time set-up per device, on the caller's current device: the device address of the
-    // fixed scratch (the array's name in host code is not a device address)
+    // set-up once per device (and again after a device reset), on the caller's current device:
+    // the device address of the fixed scratch (the array's name in host code is not a device
+    // address)
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    const unsigned long long id = current_context_id();
+    if (!g_noalloc_ptr[dev] || id == 0 || id != g_noalloc_ctx[dev]) {
       void* p = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&p, g_transform_scratch);
       if (e != cudaSuccess || p == nullptr) {
         cudaGetLastError();
+        g_noalloc_ptr[dev] = nullptr;
         return PD_ERR_CUDA;
       }
       g_noalloc_ptr[dev] = p;
+      g_noalloc_ctx[dev] = id;
     }
     base = g_noalloc_ptr[dev];
   }

@@ -38,28 +38,54 @@ def _close_rel(a, b, rel=1e-5, absf=1e-9):
     return abs(a - b) <= rel * max(abs(a), abs(b)) + absf
 
 
+def _run(B, d1, order, stream=None):
+    H, W = d1.shape
+    fitted = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    D2 = torch.full((H, W), -7.0, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    st = B.pd_transform_noalloc(d1, order, 16.0, fitted, D2, stream=stream)
+    assert st == B.PD_OK
+    torch.cuda.synchronize()
+    assert free_before - torch.cuda.mem_get_info()[0] < (2 << 20)   # no device allocation
+    return fitted, D2
+
+
 @pytest.mark.parametrize("order", [2, 1])
-def test_noalloc_transform_matches_the_context_version(B, order):
+def test_noalloc_transform_matches_the_context_version(orc, B, order):
+    """The entry point runs the very kernels of pd_transform on the same data, so the road model
+    and D2 are the same bits; the fit also agrees with the oracle (1e-5 relative, D2 1e-4 px).
+    Three calls in a row: 640x480, 1280x720 and 2048x2048 (the 4 Mpixel limit)."""
     ctx = B.Context(0)
-    cases = [_d1(101, 640, 480), _d1(202, 1280, 720)]
-    for D1 in cases:                       # two calls in a row, different sizes and data
+    for D1 in [_d1(101, 640, 480), _d1(202, 1280, 720), _d1(303, 2048, 2048)]:
         d1 = torch.from_numpy(D1).cuda()
         fitted_ref, D2_ref = B.pd_transform(ctx, d1, order, 16.0)
-        fitted = torch.zeros(fitted_ref.shape, dtype=torch.uint8, device="cuda")
-        D2 = torch.full(D2_ref.shape, -7.0, dtype=torch.float32, device="cuda")
-        torch.cuda.synchronize()
-        free_before = torch.cuda.mem_get_info()[0]
-        st = B.pd_transform_noalloc(d1, order, 16.0, fitted, D2)
-        assert st == B.PD_OK
-        torch.cuda.synchronize()
-        assert free_before - torch.cuda.mem_get_info()[0] < (2 << 20)   # no device allocation
-        m_ref = B.RoadModel.from_tensor(fitted_ref)
+        fitted, D2 = _run(B, d1, order)
+        n = len(bytes(B.RoadModel()))
+        assert torch.equal(fitted[:n], fitted_ref[:n])
+        assert torch.equal(D2, D2_ref)
         m = B.RoadModel.from_tensor(fitted)
         assert m.order == order
-        assert _close_rel(m.roll, m_ref.roll, absf=1e-8)
+        fit_o = orc.fit_road(orc.moments(D1), order)
+        assert _close_rel(m.roll, fit_o.roll, absf=1e-8)
         for i in range(order + 1):
-            assert _close_rel(m.a[i], m_ref.a[i])
-        assert torch.max(torch.abs(D2 - D2_ref)).item() <= 1e-4
+            assert _close_rel(m.a[i], fit_o.a[i])
+        D2_o = orc.transform(D1, fit_o, 16.0)
+        assert np.max(np.abs(D2.cpu().numpy() - D2_o)) <= 1e-4
+    ctx.close()
+
+
+def test_noalloc_transform_on_a_side_stream(B):
+    """Enqueued on a stream other than the current one, the call gives the same bits."""
+    ctx = B.Context(0)
+    d1 = torch.from_numpy(_d1(404, 960, 540)).cuda()
+    fitted_ref, D2_ref = B.pd_transform(ctx, d1, 2, 16.0)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    fitted, D2 = _run(B, d1, 2, stream=side)
+    n = len(bytes(B.RoadModel()))
+    assert torch.equal(fitted[:n], fitted_ref[:n])
+    assert torch.equal(D2, D2_ref)
     ctx.close()
 
 
