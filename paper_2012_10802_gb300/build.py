@@ -13,7 +13,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpothole.so")
-SOURCES = ["api.cu", "sgm.cu", "dt.cu", "detect.cu", "batch.cu", "band.cu", "cnn.cu", "ccl.cu", "report.cu"]
+SOURCES = ["api.cu", "sgm.cu", "dt.cu", "detect.cu", "batch.cu", "band.cu", "cnn.cu", "ccl.cu", "report.cu",
+           "intrate.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC,-O2",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
@@ -35,9 +36,10 @@ def _stale(target, deps):
 
 def build(force=False, verbose=False, extra=()):
     os.makedirs(OUT, exist_ok=True)
-    headers = [os.path.join(CSRC, "common.cuh"), os.path.join(CSRC, "sgm_body.cuh"),
-               os.path.join(CSRC, "batch.cuh"),
-               os.path.join(ROOT, "include", "pothole.h")]
+    # every header of the library is a dependency of every object (a handful of files)
+    inc = os.path.join(ROOT, "include")
+    headers = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h")))
+    headers += sorted(os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h"))
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
