@@ -25,11 +25,20 @@ sys.path.insert(0, ROOT)
 W_, H_, D_, PATHS_ = 1280, 720, 128, 8
 WORKLOAD = "road_1280x720_d128_8paths: warp+SGM+transform+SLIC(1000,10,10)+threshold+mask+components"
 METRIC = "SGM Mdisp/s (W*H*D/s) at 1280x720 D=128, 8 paths, whole path per step"
-# Aggregation ALU view: the recurrence needs 4 u16 lane-ops per (pixel, disparity, path) in the
-# packed DPX form (3-input min, add-min, add cost minus previous minimum, running min); peak = 64
-# int instructions per clock per SM (measured) x 2 u16 lanes x 152 SMs x max SM clock.
-AGG_LANE_OPS = 4
-INT_INSTR_PER_CLK_SM = 64
+# Roofline units of the method (integer SGM is bound by the integer ALUs, not by HBM):
+#  - aggregation, Eq. (8): 8 integer operations per (pixel, disparity, path): min of the d-1 and
+#    d+1 neighbours, + P1, min with L(d), min with m + P2, + cost, - m, the running minimum m(p)
+#    and the accumulation into S;
+#  - cost: 2 per (pixel, disparity) (xor, popcount); winner-take-all and right view: 2.
+#    So 8R + 4 per (pixel, disparity) for the SGM path, 8R for the aggregation kernel.
+#  - bytes: a two-sweep design hands one uint8 partial sum between the sweeps, 2 B per (pixel,
+#    disparity), plus about 12 B per pixel of images in and disparities out.
+# The integer peak is measured live (pd_int_rate: packed u16x2 DPX instructions, counted in u16
+# lanes); the theoretical SMs x 128 lanes x clock is reported beside it.
+AGG_OPS_PER_UNIT = 8          # per (pixel, disparity, path)
+PATH_EXTRA_OPS = 4            # per (pixel, disparity): cost 2 + winner-take-all 2
+PATH_BYTES_PER_PD = 2
+PATH_BYTES_PER_PIXEL = 12
 SMS = 152
 
 
@@ -51,6 +60,12 @@ def parse():
                          "banded around its full-range median (for profiling)")
     ap.add_argument("--size", default=None,
                     help="WxH of a smaller road for profiling captures (not a benchmark line)")
+    ap.add_argument("--no-full-hd", action="store_true",
+                    help="skip the 1920x1080 whole-path line")
+    ap.add_argument("--no-pt-compare", action="store_true",
+                    help="skip the with / without perspective-transformation comparison")
+    ap.add_argument("--int-peak", action="store_true",
+                    help="only measure and print the packed u16x2 integer peak (pd_int_rate)")
     return ap.parse_args()
 
 
@@ -436,6 +451,116 @@ def bench_band(B, torch, synth, steps=10, n_eval=4):
             "constant_centre_disagreement_mean": statistics.mean(const_dis)}
 
 
+def _timed_ms(torch, fn, steps, flush, warmup=3):
+    """Median CUDA-event time of fn on the current stream, L2 flushed before every call."""
+    for _ in range(warmup):
+        fn()
+    ms = []
+    for i in range(steps):
+        flush.fill_(i & 0xff)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return statistics.median(ms)
+
+
+def bench_full_hd(B, torch, synth, steps=10, cpu=True):
+    """The whole path on the 1920x1080 road (seed 3: roll drawn in +-3 deg, five potholes),
+    D = 128, 8 paths, SLIC with 1000 superpixels (compactness 10, 10 iterations, 1008 centres
+    after the grid rounding) and the adaptive threshold: frames/s, the per-stage split from the
+    library's events (captured graph, L2 flushed before each step), and the oracle's time for the
+    same frame on one core."""
+    sc = synth.road_1920x1080()
+    left_np, right_np = synth.render(sc)
+    H, W = left_np.shape
+    D = 128
+    ctx = B.Context(torch.cuda.current_device())
+    B.pd_pipeline_config(ctx, True)
+    model = B.RoadModel.make(*synth.true_model(sc))
+    params = B.default_params(D=D, paths=8, slic_K=1000, slic_m=10.0, slic_iters=10)
+    left, right = torch.from_numpy(left_np).cuda(), torch.from_numpy(right_np).cuda()
+    outs = B.make_outputs(ctx, W, H)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        B.pd_run_pipeline(ctx, left, right, model, params, outs)
+    torch.cuda.synchronize()
+    B.pd_profile_enable(ctx, True)
+    ms = []
+    for i in range(steps):
+        flush.fill_(i & 0xff)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        B.pd_run_pipeline(ctx, left, right, model, params, outs)
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    prof = B.pd_profile_read(ctx)
+    B.pd_profile_enable(ctx, False)
+    calls = max(prof["calls"], 1)
+    ctx.close()
+    t = statistics.median(ms)
+    stages = {k: prof[k] / calls for k in ("prep_ms", "aggregate_ms", "disparity_ms",
+                                           "transform_ms", "superpixel_ms", "mask_ms")}
+    sgm = stages["prep_ms"] + stages["aggregate_ms"] + stages["disparity_ms"]
+    res = {"workload": "road_1920x1080 seed 3, D=128, 8 paths, SLIC 1000/10/10 (1008 centres), "
+                       "threshold + mask + components; captured graph, L2 flushed per step",
+           "ms_per_frame": t, "frames_per_s": 1e3 / t, "Mdisp_s": W * H * D / (t * 1e-3) / 1e6,
+           "stage_ms": stages, "sgm_only_ms": sgm,
+           "sgm_only_Mdisp_s": W * H * D / (sgm * 1e-3) / 1e6, "steps": steps}
+    if cpu:
+        import oracle
+        oracle.lib()
+        p = oracle.Params(D=D, paths=8, slic_K=1000, slic_m=10.0, slic_iters=10)
+        t0 = time.perf_counter()
+        oracle.pipeline(left_np, right_np, oracle.RoadModel.make(*synth.true_model(sc)), p)
+        tc = time.perf_counter() - t0
+        res["cpu_baseline"] = {"value": W * H * D / tc / 1e6, "unit": "Mdisp/s", "cores": 1,
+                               "kind": "oracle", "frames_per_s": 1.0 / tc,
+                               "sample": "one full 1920x1080 frame, whole oracle path, %.1f s" % tc}
+    return res
+
+
+def bench_pt(B, torch, synth, steps=10):
+    """Sec. II-A at 1280x720 (the benchmark road): SGM (warp + cost + aggregation + disparity)
+    with the row shifts of the road model at D = 128 (the benchmark's range), without them
+    (kappa = 0, from the constant model f = delta_pt) at D = 128, which still holds the whole
+    road's disparity (at most about 110 px here), and with them at D = 32, the residual range
+    the shifts leave.  Times are CUDA-event medians with L2 flushed; accuracy against the
+    generator's disparity over the pixels with u >= 127 (where every variant can have a result):
+    the valid fraction, the mean |D1 - truth| of valid pixels and the share above 1 px."""
+    import numpy as np
+    sc = synth.road_1280x720()
+    left_np, right_np = synth.render(sc)
+    H, W = left_np.shape
+    ctx = B.Context(torch.cuda.current_device())
+    left, right = torch.from_numpy(left_np).cuda(), torch.from_numpy(right_np).cuda()
+    gt = torch.from_numpy(synth.gt_disparity(sc).astype(np.float32)).cuda()[:, 127:]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    pt = B.RoadModel.make(*synth.true_model(sc))
+    flat = B.RoadModel.make(1, (10.0, 0.0, 0.0), 0.0)   # f = delta_pt everywhere: kappa = 0
+    out = {}
+    for name, model, D in (("pt_d128", pt, 128), ("no_pt_d128", flat, 128), ("pt_d32", pt, 32)):
+        p = B.default_params(D=D, paths=8)
+        kap, d_int, D1 = B.pd_sgm(ctx, left, right, model, p)
+        ms = _timed_ms(torch, lambda: B.pd_sgm(ctx, left, right, model, p, kap, d_int, D1), steps,
+                       flush)
+        v = D1[:, 127:]
+        ok = v >= 0
+        err = (v[ok] - gt[ok]).abs()
+        out[name] = {"D": D, "ms": ms, "Mdisp_s": W * H * D / (ms * 1e-3) / 1e6,
+                     "frames_per_s": 1e3 / ms, "kappa_range": [int(kap.min()), int(kap.max())],
+                     "valid_fraction": ok.float().mean().item(),
+                     "mean_abs_err_px": err.mean().item(),
+                     "share_err_above_1px": (err > 1.0).float().mean().item()}
+    ctx.close()
+    out["workload"] = ("road_1280x720 seed 2, 8 paths: SGM with and without the perspective "
+                       "transformation")
+    return out
+
+
 def main():
     args = parse()
     global W_, H_
@@ -453,6 +578,14 @@ def main():
     from paper_2012_10802_gb300 import synth
 
     torch.cuda.set_device(local)
+    if args.int_peak:
+        ctx = B.Context(local)
+        with Clocks(local) as clk:
+            rate, ipc = B.pd_int_rate(ctx)
+        ctx.close()
+        print(json.dumps({"pd_int_rate_lane_ops_per_s": rate, "T_lane_ops_per_s": rate / 1e12,
+                          "thread_instr_per_clk_per_sm": ipc, "clocks": clk.summary()}))
+        return
     if args.band_size:
         return band_only(B, torch, synth, args.band_size, args.steps, max(args.warmup, 3))
     dist = None
@@ -516,15 +649,19 @@ def main():
             B.pd_run_pipeline(ctx, ld, rd, model, params, outs)
             mh.copy_(outs[1]["mask"], non_blocking=True)
         barrier()
-        e0.record()
-        for _ in range(args.steps):
+        e2e_local = 0.0
+        for i in range(args.steps):
+            flush.fill_((i + 7) & 0xff)            # L2 flushed before each step, as above
+            e0.record()
             ld.copy_(lh, non_blocking=True)
             rd.copy_(rh, non_blocking=True)
             B.pd_run_pipeline(ctx, ld, rd, model, params, outs)
             mh.copy_(outs[1]["mask"], non_blocking=True)
-        e1.record()
+            e1.record()
+            e1.synchronize()
+            e2e_local += e0.elapsed_time(e1)
         barrier()
-        e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+        e2e_ms = max_over_ranks(e2e_local, dist, "cuda")
         e2e = {"value": whole_job_mdisp(args.steps, world, W_, H_, D_, e2e_ms),
                "unit": "Mdisp/s", "h2d_bytes_per_step": 2 * W_ * H_,
                "d2h_bytes_per_step": W_ * H_, "ms_per_step": e2e_ms / args.steps}
@@ -540,26 +677,47 @@ def main():
     calls = max(prof["calls"], 1)
     agg_ms = prof["aggregate_ms"] / calls
     sgm_ms = (prof["prep_ms"] + prof["aggregate_ms"] + prof["disparity_ms"]) / calls
-    units = W_ * H_ * D_ * PATHS_
-    sm_max = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
-    peak_lane_ops = INT_INSTR_PER_CLK_SM * 2 * SMS * sm_max * 1e6
-    # The aggregation kernel reads one cost byte and writes one L byte per (pixel, disparity,
-    # direction): 2 bytes per unit is its algorithmic traffic, and it is bound by HBM.
-    agg_bytes = 2 * units
+    # the integer peak, measured now on this GPU (packed u16x2 DPX instructions, u16 lanes)
+    int_rate, int_ipc = B.pd_int_rate(ctx)
+    sm_mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    pd_units = W_ * H_ * D_
+    agg_ops = AGG_OPS_PER_UNIT * PATHS_ * pd_units
+    path_ops = (AGG_OPS_PER_UNIT * PATHS_ + PATH_EXTRA_OPS) * pd_units
+    path_bytes = PATH_BYTES_PER_PD * pd_units + PATH_BYTES_PER_PIXEL * W_ * H_
     hbm_peak = peaks.get("hbm_gbs") or 6800.0
-    achieved_gbs = agg_bytes / (agg_ms * 1e-3) / 1e9
-    roofline = {"kernel": "k_aggregate (Eq. 8, all 8 directions, one launch)", "bound": "hbm",
-                "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved_gbs / hbm_peak, "traffic": agg_traffic_record(),
-                "algorithmic_bytes_per_launch": agg_bytes, "avg_launch_ms": agg_ms,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks.get("hbm_gbs")
-                else "fallback 6800 GB/s",
-                "alu_view": {"lane_ops_per_launch": AGG_LANE_OPS * units,
-                             "achieved_T": AGG_LANE_OPS * units / (agg_ms * 1e-3) / 1e12,
-                             "peak_T": peak_lane_ops / 1e12,
-                             "frac": AGG_LANE_OPS * units / (agg_ms * 1e-3) / peak_lane_ops,
-                             "peak_source": "64 int instr/clk/SM (microbenchmark) x 2 u16 lanes "
-                                            "x 152 SMs x %.0f MHz" % sm_max}}
+    hbm_src = ("MEASURED_PEAKS.json hbm_gbs (measured)" if peaks.get("hbm_gbs")
+               else "fallback 6800 GB/s (no MEASURED_PEAKS.json on this box)")
+
+    def frac(ops, nbytes, ms):
+        """max(bytes / HBM peak, ops / integer peak) over the measured time."""
+        return max(nbytes / (hbm_peak * 1e9), ops / int_rate) / (ms * 1e-3)
+
+    # this design's own traffic: one cost byte in and one L byte out per (pixel, disparity, path)
+    design_bytes = 2 * PATHS_ * pd_units
+    roofline = {"kernel": "k_aggregate (Eq. 8, all 8 directions, one launch)", "bound": "alu",
+                "achieved": agg_ops / (agg_ms * 1e-3) / 1e12, "peak": int_rate / 1e12,
+                "unit": "T int-ops/s (u16 lanes)", "frac": frac(agg_ops, path_bytes, agg_ms),
+                "traffic": agg_traffic_record(),
+                "algorithmic_ops_per_launch": agg_ops,
+                "algorithmic_ops_per_unit": "8 per (pixel, disparity, path)",
+                "algorithmic_bytes_per_launch": path_bytes, "avg_launch_ms": agg_ms,
+                "peak_source": "measured live: pd_int_rate, packed u16x2 DPX, %.1f thread "
+                               "instr/clk/SM x 2 lanes, at the run's clock" % int_ipc,
+                "theoretical_peak": SMS * 128 * sm_mhz * 1e6 / 1e12,
+                "theoretical_source": "152 SMs x 128 u16 lanes/clk x %.0f MHz (median SM clock)"
+                                      % sm_mhz,
+                "hbm_view": {"design_bytes_per_launch": design_bytes,
+                             "design_GBs": design_bytes / (agg_ms * 1e-3) / 1e9,
+                             "peak_GBs": hbm_peak, "peak_source": hbm_src,
+                             "frac_of_hbm": design_bytes / (agg_ms * 1e-3) / 1e9 / hbm_peak},
+                "path": {"scope": "SGM a1-a5: row shifts, warp, census, cost, aggregation, "
+                                  "winner-take-all, sub-pixel, right view, LR check",
+                         "bound": "alu", "ops": path_ops,
+                         "ops_per_unit": "8R + 4 = %d per (pixel, disparity)"
+                                         % (AGG_OPS_PER_UNIT * PATHS_ + PATH_EXTRA_OPS),
+                         "bytes": path_bytes, "ms": sgm_ms,
+                         "achieved": path_ops / (sgm_ms * 1e-3) / 1e12,
+                         "frac": frac(path_ops, path_bytes, sgm_ms)}}
 
     # Sec. III accuracy of the benchmark frame against the generator's ground truth: disparity
     # D1 against the true disparity, mask against the pixels deeper than delta_PD
@@ -582,6 +740,12 @@ def main():
     stream_res = None
     if not args.no_stream and not args.size and rank == 0:
         stream_res = bench_stream(B, torch, synth, graph=not args.no_graph)
+    full_hd = None
+    if not args.no_full_hd and not args.size and rank == 0:
+        full_hd = bench_full_hd(B, torch, synth, cpu=not args.no_cpu_baseline)
+    pt_res = None
+    if not args.no_pt_compare and not args.size and rank == 0:
+        pt_res = bench_pt(B, torch, synth)
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -606,7 +770,7 @@ def main():
                                                             "disparity_ms", "transform_ms",
                                                             "superpixel_ms", "mask_ms")},
                    "wall_s": wall, "accuracy": acc, "batch64": batch, "band1080": band_res,
-                   "stream720": stream_res},
+                   "stream720": stream_res, "full_hd": full_hd, "pt720": pt_res},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": prof["launches"], "clocks": clocks,
     }
