@@ -156,6 +156,7 @@ struct SgmScratch {
   float* dsub;
   uint32_t* rkeys;
   int32_t* kappa;
+  unsigned int* counter;  // task counter of the persistent aggregation
 };
 
 size_t sgm_scratch_bytes(int W, int H, int D, int paths) {
@@ -167,6 +168,7 @@ size_t sgm_scratch_bytes(int W, int H, int D, int paths) {
   carve_size<float>(acc, N);
   carve_size<uint32_t>(acc, N);
   carve_size<int32_t>(acc, H);
+  carve_size<unsigned int>(acc, 1);
   return acc;
 }
 
@@ -181,6 +183,7 @@ SgmScratch sgm_carve(void* base, int W, int H, int D, int paths) {
   s.dsub = c.take<float>(N);
   s.rkeys = c.take<uint32_t>(N);
   s.kappa = c.take<int32_t>(H);
+  s.counter = c.take<unsigned int>(1);
   return s;
 }
 
@@ -215,7 +218,8 @@ pd_status sgm_enqueue(pd_ctx* ctx, const uint8_t* left, const uint8_t* right, in
   launch_cost(s, sc.cl, sc.cr, W, H, p->D, 1, sc.cost);
   cudaMemsetAsync(sc.rkeys, 0xff, N * sizeof(uint32_t), s);
   mark(ctx, rec, 1);
-  launch_aggregate(s, sc.cost, W, H, p->D, dir_set(p->paths), p->P1, p->P2, sc.vols, vol);
+  launch_aggregate_p(s, sc.cost, W, H, p->D, dir_set(p->paths), p->P1, p->P2, sc.vols, vol,
+                     sc.counter);
   mark(ctx, rec, 2);
   launch_wta(s, sc.vols, p->paths, vol, nullptr, W, H, p->D, d_int, sc.dsub, sc.rkeys);
   launch_lr(s, d_int, sc.dsub, sc.rkeys, kap, W, H, p->D, p->lr_tol, D1);
@@ -701,12 +705,14 @@ pd_status pd_aggregate_dir(pd_ctx* ctx, const uint8_t* cost, int W, int H, int D
   size_t vol = (size_t)W * H * D, need = 0;
   carve_size<uint8_t>(need, vol);
   carve_size<uint8_t>(need, vol);
+  carve_size<unsigned int>(need, 1);
   PD_TRY(ensure_ws(ctx, need));
   Carve c(ctx->ws);
   uint8_t* cil = c.take<uint8_t>(vol);
   uint8_t* lil = c.take<uint8_t>(vol);
+  unsigned int* counter = c.take<unsigned int>(1);
   launch_to_interleaved(ctx->stream, cost, (size_t)W * H, D, cil);
-  launch_aggregate(ctx->stream, cil, W, H, D, one_dir(dx, dy), P1, P2, lil, vol);
+  launch_aggregate_p(ctx->stream, cil, W, H, D, one_dir(dx, dy), P1, P2, lil, vol, counter);
   launch_to_natural(ctx->stream, lil, (size_t)W * H, D, L);
   return launched(ctx, "pd_aggregate_dir");
 }
@@ -723,12 +729,14 @@ pd_status pd_aggregate(pd_ctx* ctx, const uint8_t* cost, int W, int H, int D, in
   size_t vol = (size_t)W * H * D, need = 0;
   carve_size<uint8_t>(need, vol);
   carve_size<uint8_t>(need, vol * paths);
+  carve_size<unsigned int>(need, 1);
   PD_TRY(ensure_ws(ctx, need));
   Carve c(ctx->ws);
   uint8_t* cil = c.take<uint8_t>(vol);
   uint8_t* vols = c.take<uint8_t>(vol * paths);
+  unsigned int* counter = c.take<unsigned int>(1);
   launch_to_interleaved(ctx->stream, cost, (size_t)W * H, D, cil);
-  launch_aggregate(ctx->stream, cil, W, H, D, dir_set(paths), P1, P2, vols, vol);
+  launch_aggregate_p(ctx->stream, cil, W, H, D, dir_set(paths), P1, P2, vols, vol, counter);
   launch_sum_volumes(ctx->stream, vols, paths, vol, W, H, D, S);
   return launched(ctx, "pd_aggregate");
 }

@@ -141,8 +141,12 @@ void launch_to_interleaved(cudaStream_t s, const uint8_t* natural, size_t n_pix,
 void launch_to_natural(cudaStream_t s, const uint8_t* inter, size_t n_pix, int D, uint8_t* out);
 // Eq. (8) for every direction of `dirs`; volume r of `out` (stride vol_bytes) receives L_r in the
 // interleaved layout.
-void launch_aggregate(cudaStream_t s, const uint8_t* cost_il, int W, int H, int D,
-                      const DirSet& dirs, int P1, int P2, uint8_t* out, size_t vol_bytes);
+// Eq. (8) over all directions of `dirs` into one interleaved L volume per direction (out + r
+// vol_bytes), as one persistent launch (longest lines first; counter: one device word of
+// scratch, reset on the stream before the launch).
+void launch_aggregate_p(cudaStream_t s, const uint8_t* cost_il, int W, int H, int D,
+                        const DirSet& dirs, int P1, int P2, uint8_t* out, size_t vol_bytes,
+                        unsigned int* counter);
 // S = sum of `ndirs` interleaved L volumes, written as natural uint16 [H][W][D].
 void launch_sum_volumes(cudaStream_t s, const uint8_t* vols, int ndirs, size_t vol_bytes, int W,
                         int H, int D, uint16_t* S);

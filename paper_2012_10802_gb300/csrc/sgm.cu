@@ -1,16 +1,25 @@
 // Sec. II-A and II-B on the GPU: row shifts (Eq. (6)), the perspective warp, census cost,
 // Eq. (8) aggregation, Eq. (9) winner-take-all with sub-pixel step and left-right check, Eq. (10).
 //
-// Aggregation design: every path of every direction is an independent dynamic-programming line.
-// A line is owned by G = D/16 lanes of a warp; each lane keeps 16 disparities as 8 packed u16x2
-// words, word j holding (d = 16g + j, d = 16g + 8 + j).  With that pairing the d-1 / d+1
-// neighbours of word j are words j-1 / j+1, so the recurrence needs no byte shuffling: per word it
-// is one 3-input min and one fused add-min (Hopper/Blackwell DPX instructions) and one three-input
-// add that adds the cost and subtracts the previous minimum, and only the two ends of a lane's
-// range cross lanes.  The matching cost is computed once per (p, d) into
-// a uint8 volume (popcount is a quarter-rate instruction) and every direction reads it with one
-// 16-byte asynchronous copy per lane and step into a shared-memory ring, kStages - 1 steps ahead.
+// Aggregation design: every path of every direction is an independent dynamic-programming line,
+// walked by a group of lanes of one warp.  Each lane keeps 16 disparities of a line per
+// 16-disparity group it owns as 8 packed u16x2 words, word j holding (d = 16g + j,
+// d = 16g + 8 + j).  With that pairing the d-1 / d+1 neighbours of word j are words j-1 / j+1, so
+// the recurrence needs no byte shuffling: per word it is one 3-input min and one fused add-min
+// (DPX instructions) and one three-input add that adds the cost and subtracts the previous
+// minimum; only the ends of a group cross to the lane's other group or to the neighbouring lane.
+// Rows take one group per lane (D/16 lanes a row, the shortest step for the longest lines),
+// columns and diagonals two groups per lane (D/32 lanes a line, fewer shuffles per disparity).
+// One persistent launch covers all directions; its warps take line groups from a counter,
+// longest first.  The matching cost is computed once per (p, d) into a uint8 volume (popcount is
+// a quarter-rate instruction) and every direction reads it through a per-warp shared-memory ring
+// of asynchronous copies, several steps ahead.
 #include <cstdio>
+#include <cstring>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "common.cuh"
 #include "sgm_body.cuh"
@@ -70,20 +79,87 @@ __global__ void __launch_bounds__(kCostThreads) k_cost_il(const uint32_t* __rest
   cost_il_block(cl, cr, W, D, cost, blockIdx.x, blockIdx.y);
 }
 
-// Directions are packed 4 bits each into `dirs` (bits 4r..4r+3 of direction r): dx + 1 in the
-// low two bits, dy + 1 in the high two.
-template <int G>
-__global__ void __launch_bounds__(kAggWarps * 32, 6) k_aggregate(const uint8_t* __restrict__ cost,
-                                                                 uint8_t* __restrict__ out, int W,
-                                                                 int H, int D, uint32_t dirs,
-                                                                 uint32_t P1x2, uint32_t K21x2,
-                                                                 size_t vol_bytes) {
-  const int r = blockIdx.y;
-  const uint32_t code = (dirs >> (4 * r)) & 0xfu;
-  const int dx = (int)(code & 3u) - 1, dy = (int)(code >> 2) - 1;
-  const int warp = threadIdx.x >> 5;
-  agg_warp<G>(cost, out + (size_t)r * vol_bytes, W, H, D, dx, dy, P1x2, K21x2,
-              (blockIdx.x * kAggWarps + warp) * (32 / G), warp);
+// Task plan of the persistent aggregation of one frame.  Tasks are groups of lines walked by one
+// warp.  The rows of the horizontal directions, the longest lines, sit at every `stride`-th
+// position of the task list, so every block draws about the same share of them and they do not
+// pile up on a few SMs; the other positions hold the columns, then the diagonals from the middle
+// outwards (longest first).
+struct AggPlan {
+  int n_h, n_v, n_d;           // line groups per direction of each class
+  int nht, nvt, ntasks;        // horizontal and vertical tasks; task count
+  int stride;                  // horizontal tasks at positions 0, stride, 2 stride, ...
+  int nh, nv, nd;              // directions present in each class
+  // byte i of each word: direction i of the class as r | (dx + 1) << 3 | (dy + 1) << 5, r its
+  // output volume (bytes, not arrays: no local-memory copy of the parameter)
+  uint32_t h_code, v_code, d_code;
+};
+
+__host__ __device__ __forceinline__ uint32_t dir_code(int r, int dx, int dy) {
+  return (uint32_t)r | ((uint32_t)(dx + 1) << 3) | ((uint32_t)(dy + 1) << 5);
+}
+
+// Group index of rank r in middle-out order over n groups: the middle one, then alternately one
+// below and one above, then the rest of the longer side.
+__device__ __forceinline__ int middle_out(int r, int n) {
+  const int mid = (n - 1) >> 1;
+  if (r == 0) return mid;
+  const int below = mid, above = n - 1 - mid;
+  const int both = min(below, above);
+  const int i = r - 1;
+  if (i < 2 * both) return (i & 1) ? mid + 1 + (i >> 1) : mid - 1 - (i >> 1);
+  const int j = i - 2 * both;
+  return below > above ? mid - 1 - both - j : mid + 1 + both + j;
+}
+
+constexpr int kAggPWarps = 4;               // warps per block of the persistent aggregation
+constexpr int kAggPRingUint4 = 512;         // 8 KB ring per warp
+
+// Persistent aggregation of Eq. (8) over all directions of a frame.  Each warp repeatedly takes
+// the next task from the counter; rows are walked with GH = D/16 lanes of one 16-disparity group
+// each, columns and diagonals with GO = D/32 lanes of two groups each.
+template <int GH, int GO>
+__global__ void __launch_bounds__(kAggPWarps * 32) k_aggregate_p(
+    const uint8_t* __restrict__ cost, uint8_t* __restrict__ out, int W, int H, int D,
+    AggPlan plan, uint32_t P1x2, uint32_t K21x2, size_t vol_bytes,
+    unsigned int* __restrict__ counter) {
+  extern __shared__ uint4 s_ring_p[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint4* ring = s_ring_p + warp * kAggPRingUint4;
+  for (;;) {
+    unsigned int t = 0;
+    if (lane == 0) t = atomicAdd(counter, 1u);
+    t = __shfl_sync(kFull, t, 0);
+    if ((int)t >= plan.ntasks) break;
+    const int ti = (int)t;
+    uint32_t code;
+    int k, cls;
+    const int hq = ti / plan.stride;
+    if (ti % plan.stride == 0 && hq < plan.nht) {  // a horizontal task
+      cls = 0;
+      code = plan.h_code >> (8 * (hq % plan.nh));
+      k = hq / plan.nh;
+    } else {
+      const int j = ti - min(plan.nht, hq + 1);  // the other tasks in their own order
+      if (j < plan.nvt) {
+        cls = 1;
+        code = plan.v_code >> (8 * (j % plan.nv));
+        k = j / plan.nv;
+      } else {
+        cls = 2;
+        const int i = j - plan.nvt;
+        code = plan.d_code >> (8 * (i % plan.nd));
+        k = middle_out(i / plan.nd, plan.n_d);
+      }
+    }
+    uint8_t* dst = out + (size_t)(code & 7u) * vol_bytes;
+    const int dx = (int)((code >> 3) & 3u) - 1, dy = (int)((code >> 5) & 3u) - 1;
+    if (cls == 0)
+      agg_walk<GH, 1, true>(cost, dst, W, H, D, dx, 0, P1x2, K21x2, k * (32 / GH), ring);
+    else if (cls == 1)
+      agg_walk<GO, 2, true>(cost, dst, W, H, D, 0, dy, P1x2, K21x2, k * (32 / GO), ring);
+    else
+      agg_walk<GO, 2, false>(cost, dst, W, H, D, dx, dy, P1x2, K21x2, k * (32 / GO), ring);
+  }
 }
 
 __global__ void __launch_bounds__(kWtaThreads) k_wta(const uint8_t* __restrict__ vols, int ndirs,
@@ -256,31 +332,72 @@ void launch_to_natural(cudaStream_t s, const uint8_t* inter, size_t n_pix, int D
   k_to_natural<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(inter, n, out);
 }
 
-void launch_aggregate(cudaStream_t s, const uint8_t* cost_il, int W, int H, int D,
-                      const DirSet& dirs, int P1, int P2, uint8_t* out, size_t vol_bytes) {
-  int G = D / 16;
-  int maxlines = 0;
-  for (int r = 0; r < dirs.n; ++r) {
-    int n = dirs.dy[r] == 0 ? H : (dirs.dx[r] == 0 ? W : W + H - 1);
-    maxlines = n > maxlines ? n : maxlines;
+namespace {
+template <int GH, int GO>
+void launch_agg_p(cudaStream_t s, const uint8_t* cost, uint8_t* out, int W, int H, int D,
+                  const AggPlan& plan, uint32_t P1x2, uint32_t K21x2, size_t vol_bytes,
+                  unsigned int* counter) {
+  const size_t smem = (size_t)kAggPWarps * kAggPRingUint4 * sizeof(uint4);
+  const void* f = (const void*)k_aggregate_p<GH, GO>;
+  raise_smem_limit(f, smem);
+  // one wave of resident blocks: per device, the SM count times the blocks an SM holds
+  static std::mutex mu;
+  static std::map<int, int> blocks;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int nb = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = blocks.find(dev);
+    if (it == blocks.end()) {
+      int sms = 0, per = 0;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_aggregate_p<GH, GO>,
+                                                    kAggPWarps * 32, smem);
+      nb = std::max(1, sms * std::max(1, per));
+      blocks[dev] = nb;
+    } else {
+      nb = it->second;
+    }
   }
-  int lines_per_block = kAggWarps * (32 / G);
-  dim3 grid((maxlines + lines_per_block - 1) / lines_per_block, dirs.n);
-  const size_t smem = (size_t)kAggWarps * kStages * 32 * sizeof(uint4);
-  raise_smem_limit((const void*)k_aggregate<2>, smem);
-  raise_smem_limit((const void*)k_aggregate<4>, smem);
-  raise_smem_limit((const void*)k_aggregate<8>, smem);
-  raise_smem_limit((const void*)k_aggregate<16>, smem);
-  uint32_t P1x2 = (uint32_t)P1 * 0x10001u;
-  uint32_t K21x2 = (uint32_t)(P2 - P1) * 0x10001u;
-  uint32_t packed = 0;
-  for (int r = 0; r < dirs.n; ++r)
-    packed |= ((uint32_t)(dirs.dx[r] + 1) | ((uint32_t)(dirs.dy[r] + 1) << 2)) << (4 * r);
-  switch (G) {
-    case 2: k_aggregate<2><<<grid, kAggWarps * 32, smem, s>>>(cost_il, out, W, H, D, packed, P1x2, K21x2, vol_bytes); break;
-    case 4: k_aggregate<4><<<grid, kAggWarps * 32, smem, s>>>(cost_il, out, W, H, D, packed, P1x2, K21x2, vol_bytes); break;
-    case 8: k_aggregate<8><<<grid, kAggWarps * 32, smem, s>>>(cost_il, out, W, H, D, packed, P1x2, K21x2, vol_bytes); break;
-    case 16: k_aggregate<16><<<grid, kAggWarps * 32, smem, s>>>(cost_il, out, W, H, D, packed, P1x2, K21x2, vol_bytes); break;
+  nb = std::min(nb, (plan.ntasks + kAggPWarps - 1) / kAggPWarps);
+  cudaMemsetAsync(counter, 0, sizeof(unsigned int), s);
+  k_aggregate_p<GH, GO><<<nb, kAggPWarps * 32, smem, s>>>(cost, out, W, H, D, plan, P1x2,
+                                                             K21x2, vol_bytes, counter);
+}
+}  // namespace
+
+void launch_aggregate_p(cudaStream_t s, const uint8_t* cost_il, int W, int H, int D,
+                        const DirSet& dirs, int P1, int P2, uint8_t* out, size_t vol_bytes,
+                        unsigned int* counter) {
+  AggPlan plan;
+  memset(&plan, 0, sizeof(plan));
+  const int GH = D / 16, GO = D / 32;
+  const int lh = 32 / GH, lo = 32 / GO;
+  plan.n_h = (H + lh - 1) / lh;
+  plan.n_v = (W + lo - 1) / lo;
+  plan.n_d = (W + H - 1 + lo - 1) / lo;
+  for (int r = 0; r < dirs.n; ++r) {
+    const int dx = dirs.dx[r], dy = dirs.dy[r];
+    if (dy == 0)
+      plan.h_code |= dir_code(r, dx, dy) << (8 * plan.nh++);
+    else if (dx == 0)
+      plan.v_code |= dir_code(r, dx, dy) << (8 * plan.nv++);
+    else
+      plan.d_code |= dir_code(r, dx, dy) << (8 * plan.nd++);
+  }
+  plan.nht = plan.nh * plan.n_h;
+  plan.nvt = plan.nv * plan.n_v;
+  plan.ntasks = plan.nht + plan.nvt + plan.nd * plan.n_d;
+  // the last horizontal task must sit inside the list: stride * (nht - 1) < ntasks
+  plan.stride = plan.nht > 1 ? std::max(1, (plan.ntasks - 1) / (plan.nht - 1)) : 1;
+  const uint32_t P1x2 = (uint32_t)P1 * 0x10001u;
+  const uint32_t K21x2 = (uint32_t)(P2 - P1) * 0x10001u;
+  switch (D) {
+    case 32: launch_agg_p<2, 1>(s, cost_il, out, W, H, D, plan, P1x2, K21x2, vol_bytes, counter); break;
+    case 64: launch_agg_p<4, 2>(s, cost_il, out, W, H, D, plan, P1x2, K21x2, vol_bytes, counter); break;
+    case 128: launch_agg_p<8, 4>(s, cost_il, out, W, H, D, plan, P1x2, K21x2, vol_bytes, counter); break;
+    case 256: launch_agg_p<16, 8>(s, cost_il, out, W, H, D, plan, P1x2, K21x2, vol_bytes, counter); break;
     default: break;  // the API admits D in {32, 64, 128, 256} only
   }
 }

@@ -2,6 +2,8 @@
 // the batched ones (batch.cu).  Each body takes its block coordinates explicitly.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace pd {
@@ -185,8 +187,6 @@ __device__ __forceinline__ void cost_il_block(const uint32_t* __restrict__ cl,
 }
 
 // ----------------------------------------------------------------------------- Eq. (8)
-constexpr int kAggWarps = 4;
-
 constexpr int kStages = 16;  // per-warp shared-memory ring of cost rows: kStages - 1 steps in flight
 
 // Asynchronous 16-byte copy global -> shared (cp.async, L2 only); src_bytes = 0 writes zeros and
@@ -380,6 +380,170 @@ __device__ __forceinline__ void agg_warp(const uint8_t* __restrict__ cost,
     }
   }
   cp_async_wait<0>();  // no copy may still be in flight when the warp exits
+}
+
+// The walker of the persistent aggregation: like agg_warp, for lines of G lanes that each keep NG
+// consecutive 16-disparity groups (G * NG = D / 16; NG = 1 or 2), with the warp's ring passed in
+// (ring_base: ST = 16 / NG stages of 32 lanes x NG x 16 bytes, 8 KB).  With two groups a lane
+// carries 16 words: the step between its groups is a byte permutation inside the lane, so a line
+// needs half the lanes, shuffles and per-step bookkeeping of one group per lane.  FULL: every
+// line of the warp lies inside the image at every step (rows and columns), so a lane is active
+// for the whole walk when its line exists and the per-step activity tests and state resets go.
+template <int G, int NG, bool FULL>
+__device__ __forceinline__ void agg_walk(const uint8_t* __restrict__ cost,
+                                         uint8_t* __restrict__ dst_vol, int W, int H, int D,
+                                         int dx, int dy, uint32_t P1x2, uint32_t K21x2, int first,
+                                         uint4* __restrict__ ring_base) {
+  constexpr int LPW = 32 / G;  // lines per warp
+  constexpr int NW = 8 * NG;   // u16x2 words per lane
+  static_assert(NG == 1 || NG == 2, "one or two groups per lane");
+  constexpr int ST = 16 / NG;  // ring stages
+  const int nlines = dy == 0 ? H : (dx == 0 ? W : W + H - 1);
+  const int lane = threadIdx.x & 31;
+  const int g = lane % G;
+  if (first >= nlines) return;  // the whole warp leaves together
+  const int line = first + lane / G;
+  const int last = min(first + LPW, nlines) - 1;
+  const bool lvalid = line < nlines;
+  const LineWalk lw = line_walk(dx, dy, W, H, D, line, first, last, lvalid);
+  const uint8_t* csrc = cost + 16 * NG * g;
+  uint8_t* dst = dst_vol + 16 * NG * g;
+
+  uint32_t N[NW];
+#pragma unroll
+  for (int j = 0; j < NW; ++j) N[j] = 0;
+  uint32_t mp = 0;
+
+  // stage k of this lane: NG consecutive 16-byte slots at ring_base + (k * 32 + lane) * NG
+  uint4* ring = ring_base + lane * NG;
+  const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
+  long long pf_off = lw.off0;
+#pragma unroll
+  for (int k = 0; k < ST - 1; ++k) {
+    // only steps of the walk are read (a line may be shorter than the ring)
+    const bool in = FULL ? (lvalid && k < lw.nsteps) : (k >= lw.s_first && k <= lw.s_last);
+#pragma unroll
+    for (int q = 0; q < NG; ++q)
+      cp_async16(ring_s + (k * 32 * NG + q) * 16, csrc + (in ? pf_off : 0) + 16 * q,
+                 in ? 16u : 0u);
+    cp_async_commit();
+    pf_off += lw.delta;
+  }
+  long long st_off = lw.off0;
+  // Step s.  ALL: every lane's line is inside the image at this step (warp-uniform), so no
+  // activity test, select or reset is needed.
+  auto step = [&](const int s, auto all_tag) {
+    constexpr bool ALL = decltype(all_tag)::value;
+    const int k = s & (ST - 1);
+    // rows and columns: a lane is active exactly when its line exists; diagonals: inside the
+    // common range every lane is (all its lines exist there)
+    const bool act = FULL ? lvalid : (ALL || (s >= lw.s_first && s <= lw.s_last));
+    cp_async_wait<ST - 2>();  // the copy of step s is complete
+    uint32_t raw[4 * NG];
+#pragma unroll
+    for (int q = 0; q < NG; ++q) {
+      const uint4 rv = ring[k * 32 * NG + q];
+      raw[4 * q + 0] = rv.x;
+      raw[4 * q + 1] = rv.y;
+      raw[4 * q + 2] = rv.z;
+      raw[4 * q + 3] = rv.w;
+    }
+    {
+      const int sp = s + ST - 1;
+      const bool in = FULL ? (lvalid && sp < lw.nsteps) : (sp >= lw.s_first && sp <= lw.s_last);
+      const int kp = (k + ST - 1) & (ST - 1);
+#pragma unroll
+      for (int q = 0; q < NG; ++q)
+        cp_async16(ring_s + (kp * 32 * NG + q) * 16, csrc + (in ? pf_off : 0) + 16 * q,
+                   in ? 16u : 0u);
+      cp_async_commit();
+      pf_off += lw.delta;
+    }
+    uint32_t prevHi = kBig2, nextLo = kBig2;
+    if constexpr (G > 1) {
+      const uint32_t up = __shfl_up_sync(kFull, N[NW - 1], 1, G);
+      const uint32_t dn = __shfl_down_sync(kFull, N[0], 1, G);
+      if (g > 0) prevHi = up;
+      if (g < G - 1) nextLo = dn;
+    }
+    const uint32_t K = mp + K21x2;
+    uint32_t Lw[NW];
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+      const int q = j >> 3, i = j & 7;
+      // d - 1 and d + 1 neighbours: inside the group the adjacent words; at a group's ends the
+      // byte permutation with the neighbouring group (this lane's other group or the
+      // neighbouring lane's)
+      constexpr int kNW = NW;
+      const uint32_t below = N[(j + kNW - 1) % kNW], above = N[(j + 1) % kNW];
+      uint32_t lft, rgt;
+      if (i == 0)
+        lft = __byte_perm(q == 0 ? prevHi : below, N[(j + 7) % kNW], 0x5432);
+      else
+        lft = below;
+      if (i == 7)
+        rgt = __byte_perm(N[(j + kNW - 7) % kNW], q == NG - 1 ? nextLo : above, 0x5432);
+      else
+        rgt = above;
+      uint32_t t = __vimin3_u16x2(lft, rgt, K);
+      t = __viaddmin_u16x2(t, P1x2, N[j]);
+      const uint32_t c = __byte_perm(raw[j >> 1], 0, (j & 1) ? 0x4342 : 0x4140);
+      Lw[j] = t + c - mp;
+    }
+    uint32_t m;
+    if constexpr (NW == 8) {
+      m = __vimin3_u16x2(__vimin3_u16x2(Lw[0], Lw[1], Lw[2]), __vimin3_u16x2(Lw[3], Lw[4], Lw[5]),
+                         __vminu2(Lw[6], Lw[7]));
+    } else {
+      const uint32_t a = __vimin3_u16x2(Lw[0], Lw[1], Lw[2]);
+      const uint32_t b = __vimin3_u16x2(Lw[3], Lw[4], Lw[5]);
+      const uint32_t c = __vimin3_u16x2(Lw[6], Lw[7], Lw[8]);
+      const uint32_t d = __vimin3_u16x2(Lw[9], Lw[10], Lw[11]);
+      const uint32_t e = __vimin3_u16x2(Lw[12], Lw[13], Lw[14]);
+      m = __vminu2(__vimin3_u16x2(a, b, c), __vimin3_u16x2(d, e, Lw[15]));
+    }
+    m = __vminu2(m, __byte_perm(m, m, 0x1032));
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) m = __vminu2(m, __shfl_xor_sync(kFull, m, o, G));
+    if (act) {
+#pragma unroll
+      for (int q = 0; q < NG; ++q) {
+        uint4 w;
+        w.x = __byte_perm(Lw[8 * q + 0], Lw[8 * q + 1], 0x6420);
+        w.y = __byte_perm(Lw[8 * q + 2], Lw[8 * q + 3], 0x6420);
+        w.z = __byte_perm(Lw[8 * q + 4], Lw[8 * q + 5], 0x6420);
+        w.w = __byte_perm(Lw[8 * q + 6], Lw[8 * q + 7], 0x6420);
+        __stcs(reinterpret_cast<uint4*>(dst + st_off) + q, w);
+      }
+    }
+    if (FULL || ALL || act) {
+#pragma unroll
+      for (int j = 0; j < NW; ++j) N[j] = Lw[j];
+      mp = m;
+    } else {
+#pragma unroll
+      for (int j = 0; j < NW; ++j) N[j] = 0;
+      mp = 0;
+    }
+    st_off += lw.delta;
+  };
+  // The steps where every lane of the warp is active: all of them for rows and columns (FULL);
+  // for diagonals the common part of the lines' ranges, almost the whole walk, as the warp's lines
+  // are adjacent diagonals.  Steps outside it keep the per-lane activity test.
+  int s_all_lo = 0, s_all_hi = lw.nsteps - 1;
+  if constexpr (!FULL) {
+    s_all_lo = __reduce_max_sync(kFull, lw.s_first);
+    s_all_hi = __reduce_min_sync(kFull, lw.s_last);  // -1 when some lane has no line
+    if (s_all_hi < s_all_lo) s_all_lo = s_all_hi = lw.nsteps;  // no common range
+  }
+  int s = 0;
+  for (; s < s_all_lo; ++s) step(s, std::false_type{});
+  // a 2x unrolled loop with a run-time ring slot keeps the code small: the persistent kernel
+  // holds three variants of this walk, and fully unrolled they missed the instruction cache
+#pragma unroll 2
+  for (; s <= s_all_hi && s < lw.nsteps; ++s) step(s, std::true_type{});
+  for (; s < lw.nsteps; ++s) step(s, std::false_type{});
+  cp_async_wait<0>();  // no copy may still be in flight when the walk ends
 }
 
 // ------------------------------------------------------------- volume sums and Eq. (9)
