@@ -423,6 +423,30 @@ pd_status pd_cnn_loss_grad(pd_ctx* ctx, pd_cnn* net, const void* x, const float*
 pd_status pd_cnn_train_step(pd_ctx* ctx, pd_cnn* net, const void* x, const float* targets, int B,
                             int Hd, int Wd, float lr, float* loss);
 
+/* Training checkpoints of the band network (a file format of this library; the paper trains no
+ * network).  Layout, all little-endian: the magic "PDCNNCK" and a NUL byte, u32 format version
+ * (1), u32 parameter count n, u64 Adam step count, u64 caller-state byte count r, f32[n] master
+ * parameters, f32[n] Adam first moments, f32[n] Adam second moments, the r caller-state bytes,
+ * and a u32 CRC-32 (IEEE 802.3 / zlib) of every byte before it.  The caller state is opaque to
+ * the library (for instance the state of the training loop's random generator), r <= 1 MiB.
+ * Training is bit-reproducible (the gradient sums run in a fixed order), so training N steps,
+ * saving, loading into a fresh network and training M more gives the bits of N + M steps.
+ *  - pd_cnn_save downloads the state (synchronising ctx's stream) and writes `path` through a
+ *    temporary file "<path>.tmp" renamed over it.  PD_ERR_INVALID_ARG if it cannot be written.
+ *  - pd_cnn_load checks the file (magic, version, n equal to pd_cnn_num_params(), size, CRC)
+ *    before touching the network; a failed check returns PD_ERR_INVALID_ARG and leaves it
+ *    unchanged.  Then it restores parameters, moments and step, refreshes the bf16 weights and
+ *    synchronises ctx's stream.  state (may be NULL) receives min(state_cap, r) caller-state bytes,
+ *    *state_bytes (may be NULL) is set to r.
+ *  - pd_cnn_checkpoint_info runs the same checks on the host alone (no device or context) and
+ *    reports n, the step and r; PD_ERR_INVALID_ARG for a missing or damaged file. */
+pd_status pd_cnn_save(pd_ctx* ctx, pd_cnn* net, const char* path, const void* state,
+                      size_t state_bytes);
+pd_status pd_cnn_load(pd_ctx* ctx, pd_cnn* net, const char* path, void* state, size_t state_cap,
+                      size_t* state_bytes);
+pd_status pd_cnn_checkpoint_info(const char* path, int* n_params, long long* step,
+                                 size_t* state_bytes);
+
 /* The network input of one pair: the right image shifted row by row as in Sec. II-A
  * (right(clamp(u - kappa(v)))), both images summed over 4x4 blocks (edge rows and columns
  * repeated), mapped to (sum - 2048) / 1024 and rounded to bf16.  x: bf16 [Hd][Wd][2] (device). */

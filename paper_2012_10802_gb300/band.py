@@ -64,19 +64,29 @@ def make_training_set(B, ctx, n_pairs, W=1920, H=1080, D=128, seed0=TRAIN_SEED0,
     return X, T
 
 
-def train(B, ctx, net, X, T, steps, batch=16, lr=2e-3, seed=0, log=None):
-    """Adam over random minibatches; the step size falls by 10x over the last quarter."""
+def train(B, ctx, net, X, T, steps, batch=16, lr=2e-3, seed=0, log=None, first=0, stop=None,
+          checkpoint=None, resume=False):
+    """Adam over random minibatches; the step size falls by 10x over the last quarter of `steps`.
+    Runs steps first .. stop - 1 (stop defaults to `steps`).  checkpoint: a file path; with
+    resume=True the network, the Adam state and the minibatch generator are restored from it and
+    training continues from its step; at the end the state is saved there.  Training is
+    bit-reproducible, so a run split at any step gives the bits of an unbroken one."""
     import torch
 
     n = X.shape[0]
     g = torch.Generator(device="cpu")
     g.manual_seed(seed)
+    if resume:
+        state = B.pd_cnn_load(ctx, net, checkpoint)
+        g.set_state(torch.frombuffer(bytearray(state), dtype=torch.uint8))
+        first = B.pd_cnn_checkpoint_info(checkpoint)["step"]
+    stop = steps if stop is None else stop
     loss = torch.zeros(1, dtype=torch.float32, device=ctx.device)
     xb = torch.empty((batch,) + tuple(X.shape[1:]), dtype=X.dtype, device=ctx.device)
     tb = torch.empty((batch,) + tuple(T.shape[1:]), dtype=T.dtype, device=ctx.device)
     history = []
     t0 = time.time()
-    for s in range(steps):
+    for s in range(first, stop):
         idx = torch.randint(0, n, (batch,), generator=g).to(ctx.device)
         torch.index_select(X, 0, idx, out=xb)
         torch.index_select(T, 0, idx, out=tb)
@@ -87,6 +97,8 @@ def train(B, ctx, net, X, T, steps, batch=16, lr=2e-3, seed=0, log=None):
             if log and (s + 1) % 500 == 0:
                 log("step %d loss %.4f (%.1f s)" % (s + 1, history[-1][1], time.time() - t0))
     torch.cuda.synchronize()
+    if checkpoint:
+        B.pd_cnn_save(ctx, net, checkpoint, g.get_state().numpy().tobytes())
     return history
 
 
@@ -111,6 +123,12 @@ def main(argv=None):
     tr.add_argument("--lr", type=float, default=2e-3)
     tr.add_argument("--seed", type=int, default=0)
     tr.add_argument("--out", default=WEIGHTS)
+    tr.add_argument("--checkpoint", default=None,
+                    help="training checkpoint file, written at the end (and read with --resume)")
+    tr.add_argument("--resume", action="store_true",
+                    help="continue from --checkpoint: network, Adam state and minibatch generator")
+    tr.add_argument("--stop", type=int, default=None,
+                    help="stop before this step (then --resume continues the same schedule)")
     a = ap.parse_args(argv)
 
     import torch
@@ -123,7 +141,8 @@ def main(argv=None):
     log("targets: %.3f of tiles confident, %.3f with a centre" % (conf, T[..., 2].mean().item()))
     net = B.Cnn(0, max_batch=a.batch, max_hd=X.shape[1], max_wd=X.shape[2])
     B.pd_cnn_set_params(ctx, net, init_params(a.seed))
-    hist = train(B, ctx, net, X, T, a.steps, a.batch, a.lr, a.seed, log)
+    hist = train(B, ctx, net, X, T, a.steps, a.batch, a.lr, a.seed, log, stop=a.stop,
+                 checkpoint=a.checkpoint, resume=a.resume)
     params = B.pd_cnn_get_params(ctx, net)
     os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
     np.savez(a.out, params=params, history=np.array(hist, np.float64),

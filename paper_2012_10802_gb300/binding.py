@@ -128,6 +128,10 @@ SIGNATURES = {
     "pd_pipeline_config": [_P, _i],
     "pd_profile_read": [_P, C.POINTER(Profile)],
     "pd_int_rate": [_P, _i, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+    "pd_cnn_save": [_P, _P, C.c_char_p, _P, C.c_size_t],
+    "pd_cnn_load": [_P, _P, C.c_char_p, _P, C.c_size_t, C.POINTER(C.c_size_t)],
+    "pd_cnn_checkpoint_info": [C.c_char_p, C.POINTER(C.c_int), C.POINTER(C.c_longlong),
+                               C.POINTER(C.c_size_t)],
 }
 EXTRA = {"pd_last_error": (C.c_char_p, [_P]), "pd_workspace_bytes": (C.c_size_t, [_P]),
          "pd_cnn_num_params": (C.c_int, [])}
@@ -377,6 +381,34 @@ def pd_cnn_get_params(ctx, net):
     a = np.empty(pd_cnn_num_params(), np.float32)
     ctx.check(lib().pd_cnn_get_params(ctx.h, net.h, a.ctypes.data_as(C.c_void_p), a.size))
     return a
+
+
+def pd_cnn_save(ctx, net, path, state=b""):
+    """Writes the network's training checkpoint (parameters, Adam moments and step) with `state`,
+    opaque caller bytes such as the training loop's generator state (see include/pothole.h)."""
+    state = bytes(state)
+    buf = C.create_string_buffer(state, len(state)) if state else None
+    ctx.check(lib().pd_cnn_save(ctx.h, net.h, os.fsencode(path), buf, len(state)))
+
+
+def pd_cnn_load(ctx, net, path):
+    """Restores a checkpoint written by pd_cnn_save; returns the caller-state bytes saved with it."""
+    n = C.c_size_t(0)
+    info = pd_cnn_checkpoint_info(path)
+    cap = info["state_bytes"] if info else 0
+    buf = C.create_string_buffer(max(cap, 1))
+    ctx.check(lib().pd_cnn_load(ctx.h, net.h, os.fsencode(path), buf, cap, C.byref(n)))
+    return buf.raw[:n.value]
+
+
+def pd_cnn_checkpoint_info(path):
+    """Host-only check of a checkpoint file: {"n_params", "step", "state_bytes"}, or None when the
+    file is missing or damaged (wrong magic, version, size or CRC)."""
+    n, step, sb = C.c_int(0), C.c_longlong(0), C.c_size_t(0)
+    st = lib().pd_cnn_checkpoint_info(os.fsencode(path), C.byref(n), C.byref(step), C.byref(sb))
+    if st != PD_OK:
+        return None
+    return {"n_params": n.value, "step": step.value, "state_bytes": sb.value}
 
 
 def _out_shape(Hd, Wd):

@@ -7,11 +7,16 @@
 // NHWC.  Every contraction runs on the fifth-generation tensor cores (bf16 operands in shared
 // memory, fp32 accumulators in tensor memory, one issuing thread per CTA): each convolution is an
 // implicit GEMM over the patch matrix (k = (ky * 3 + kx) * Cin + ci), and the backward pass computes
-// dW = dZ^T Col (split over pixels, fp32 atomics) and dCol = dZ W with operands read in place
+// dW = dZ^T Col (split over pixels, partial sums added in a fixed order) and dCol = dZ W with
+// operands read in place
 // (MN-major where the contraction runs along their rows), then a gather col2im that applies the
 // previous layer's ReLU mask.  Training is Adam on fp32 master weights.
 #include <math.h>
 #include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
 #include <string.h>
 
 #include <algorithm>
@@ -299,8 +304,10 @@ __global__ void __launch_bounds__(kBwdThreads) k_dcol_tc(DcolArgs a) {
   }
 }
 
-// dW[co][k] += sum over one pixel range of Col[p][k] dZ[p][co].  Grid: (pixel ranges, k-tiles of
-// 128); the CTA accumulates D[k][co] in TMEM over 64-pixel stages and adds it to dW with atomics.
+// part[r][co][k] = sum over pixel range r of Col[p][k] dZ[p][co].  Grid: (pixel ranges, k-tiles of
+// 128); the CTA accumulates D[k][co] in TMEM over 64-pixel stages and writes its range's partial
+// sums; k_sum_ranges then adds the ranges in a fixed order (no atomics: training is
+// bit-reproducible run to run).
 //  * A = Col read MN-major: a core-matrix row is 8 consecutive k of one pixel, k-group kg and
 //    pixel-group pg of a stage at kg * 1024 + pg * 128;
 //  * B = dZ read MN-major likewise (co-groups; those beyond ldz zero);
@@ -310,7 +317,7 @@ struct DwArgs {
   int kp;                    // 32 or 288
   const __nv_bfloat16* dZ;   // [P][ldz]
   int ldz;
-  float* dW;  // [coutp][kp], accumulated
+  float* part;  // [ranges][coutp][kp]: this CTA's pixel range's partial sums
   int coutp;
   int* status;
   int P, chunk;  // pixels per CTA, a multiple of 64
@@ -318,6 +325,7 @@ struct DwArgs {
 };
 
 constexpr int kDwStage = 64;
+constexpr int kBiasBlocks = 2048;  // at most this many blocks sum the bias gradient
 constexpr size_t dw_smem_bytes(int n) { return 2 * (size_t)(16 + n / 8) * 1024; }
 
 template <int N>  // co columns: 32, or 16 for the output layer
@@ -400,7 +408,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_dw_tc(DwArgs a) {
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const int co = 16 * half + i;
-        if (co < a.coutp) atomicAdd(a.dW + (size_t)co * a.kp + k, __uint_as_float(r[i]));
+        if (co < a.coutp)
+          a.part[((size_t)blockIdx.x * a.coutp + co) * a.kp + k] = __uint_as_float(r[i]);
       }
   }
   tc::fence_before_sync();
@@ -419,15 +428,29 @@ void dcol_tc(cudaStream_t s, const DcolArgs& a) {
   k_dcol_tc<<<(a.P + kConvM - 1) / kConvM, kBwdThreads, dcol_smem_bytes(), s>>>(a);
 }
 
-// Pixel ranges sized for about two CTAs per SM over all k-tiles.
+// out[i] = sum over r = 0 .. ranges - 1 of part[r][i], in that order.
+__global__ void k_sum_ranges(const float* __restrict__ part, int ranges, int n,
+                             float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float acc = 0.0f;
+  for (int r = 0; r < ranges; ++r) acc += part[(size_t)r * n + i];
+  out[i] = acc;
+}
+
+// Pixel ranges sized for about two CTAs per SM over all k-tiles (at most 2 sms ranges, the rows
+// of the partial-sum buffer); dW = the ranges' sum.
 template <int N>
-void dw_tc(cudaStream_t s, DwArgs a, int sms) {
+void dw_tc(cudaStream_t s, DwArgs a, int sms, float* dW) {
   const int ktiles = (a.kp + 127) / 128;
   const int ranges = std::max(1, 2 * sms / ktiles);
   a.chunk = std::max(kDwStage, ((a.P + ranges - 1) / ranges + kDwStage - 1) / kDwStage * kDwStage);
   raise_smem_limit((const void*)k_dw_tc<N>, dw_smem_bytes(N));
-  dim3 grid((a.P + a.chunk - 1) / a.chunk, ktiles);
+  const int used = (a.P + a.chunk - 1) / a.chunk;  // <= ranges
+  dim3 grid(used, ktiles);
   k_dw_tc<N><<<grid, kBwdThreads, dw_smem_bytes(N), s>>>(a);
+  const int n = a.coutp * a.kp;
+  k_sum_ranges<<<(n + 255) / 256, 256, 0, s>>>(a.part, used, n, dW);
 }
 
 // dA(b, y, x, c) = mask(b, y, x, c) * sum over taps with oy = (y + 1 - ky) / s, ox = (x + 1 - kx) / s
@@ -477,9 +500,10 @@ __global__ void k_col2im32(const float* __restrict__ dcol, const __nv_bfloat16* 
   }
 }
 
-// db[c] += sum over rows of dZ[p][c] (C channels, ld columns per row).
+// part[b][c] = sum over block b's rows of dZ[p][c] (C channels, ld columns per row); the blocks'
+// sums are then added in block order by k_sum_ranges.
 __global__ void k_bias_grad(const __nv_bfloat16* __restrict__ dZ, size_t P, int C, int ld,
-                            float* __restrict__ db) {
+                            float* __restrict__ out_part) {
   __shared__ float part[256];
   const int c = threadIdx.x % C;
   const int rows_per_pass = blockDim.x / C;
@@ -492,7 +516,7 @@ __global__ void k_bias_grad(const __nv_bfloat16* __restrict__ dZ, size_t P, int 
   if ((int)threadIdx.x < C) {
     float t = 0.0f;
     for (int r = 0; r < rows_per_pass; ++r) t += part[r * C + threadIdx.x];
-    atomicAdd(db + threadIdx.x, t);
+    out_part[(size_t)blockIdx.x * C + threadIdx.x] = t;
   }
 }
 
@@ -723,6 +747,8 @@ struct pd_cnn {
   __nv_bfloat16* wb = nullptr;
   float* dW = nullptr;
   float* db = nullptr;
+  float* part = nullptr;     // partial gradient sums: [2 sms][32][288] floats
+  int sms = 0;               // SM count of the device (sizes the weight-gradient pixel ranges)
   float* scal = nullptr;     // loss, n_c, n_b
   int* status = nullptr;     // bit 0: a tensor-core wait of the convolutions ran out
   int step = 0;
@@ -846,17 +872,18 @@ void cnn_backward(cudaStream_t s, pd_cnn* net, int B, const Shapes& sh, int sms)
     w.kp = L.kp;
     w.dZ = dz[l];
     w.ldz = ldz;
-    w.dW = net->dW + L.dw_off;
+    w.part = net->part;
     w.coutp = L.coutp;
     w.status = net->status;
     w.P = P;
     w.wait_limit = kConvWaitCycles;
-    if (l == 3) dw_tc<16>(s, w, sms);
-    else dw_tc<32>(s, w, sms);
+    if (l == 3) dw_tc<16>(s, w, sms, net->dW + L.dw_off);
+    else dw_tc<32>(s, w, sms, net->dW + L.dw_off);
     {
       const int threads = 256;
-      const int blocks = (int)std::min<size_t>(((size_t)P * ldz + 4095) / 4096 + 1, 2048);
-      k_bias_grad<<<blocks, threads, 0, s>>>(dz[l], P, L.cout, ldz, net->db + L.db_off);
+      const int blocks = (int)std::min<size_t>(((size_t)P * ldz + 4095) / 4096 + 1, kBiasBlocks);
+      k_bias_grad<<<blocks, threads, 0, s>>>(dz[l], P, L.cout, ldz, net->part);
+      k_sum_ranges<<<1, 32, 0, s>>>(net->part, blocks, L.cout, net->db + L.db_off);
     }
     if (l == 0) break;
     // dCol[p][k] = sum_co dZ[p][co] W[co][k]
@@ -909,7 +936,7 @@ pd_status loss_grad_enqueue(pd_ctx* ctx, pd_cnn* net, const __nv_bfloat16* x, co
   cudaMemsetAsync(net->scal, 0, 4 * sizeof(float), s);
   k_loss_counts<<<grid_for(P4, 256), 256, 0, s>>>(tgt, P4, net->scal + 1);
   k_loss<<<grid_for(P4, 256), 256, 0, s>>>(net->out, tgt, P4, net->scal + 1, net->dz4, net->scal);
-  cnn_backward(s, net, B, sh, ctx->sm_count > 0 ? ctx->sm_count : 152);
+  cnn_backward(s, net, B, sh, net->sms);
   return PD_OK;
 }
 
@@ -984,6 +1011,13 @@ pd_status pd_cnn_create(pd_cnn** out, int device, int max_batch, int max_hd, int
   alloc(net->wb, net->wb_elems);
   alloc(net->dW, net->dw_elems);
   alloc(net->db, 4 * 32);
+  if (cudaDeviceGetAttribute(&net->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      net->sms < 1) {
+    cudaGetLastError();
+    net->sms = 1;
+  }
+  // weight-gradient ranges (at most 2 sms rows of coutp x kp <= 32 x 288) and bias-gradient blocks
+  alloc(net->part, std::max((size_t)2 * net->sms * 32 * 288, (size_t)kBiasBlocks * 32));
   alloc(net->scal, 4);
   alloc(net->status, 1);
   alloc(net->x0, P[0] * 2);
@@ -1024,6 +1058,7 @@ pd_status pd_cnn_destroy(pd_cnn* net) {
   if (!net) return PD_OK;
   cudaSetDevice(net->device);
   void* ptrs[] = {net->theta, net->adam_m, net->adam_v, net->bias, net->wb, net->dW, net->db,
+                  net->part,
                   net->scal, net->status, net->x0, net->a1, net->a2, net->a3, net->col1, net->col2, net->col3,
                   net->col4, net->dz1, net->dz2, net->dz3, net->dz4, net->out, net->dcol};
   for (void* p : ptrs)
@@ -1033,6 +1068,229 @@ pd_status pd_cnn_destroy(pd_cnn* net) {
 }
 
 int pd_cnn_num_params(void) { return make_desc().n_params; }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------ training checkpoints
+// File layout, all little-endian: magic "PDCNNCK" NUL (8 bytes), u32 format version, u32
+// parameter count n, u64 Adam step, u64 caller-state byte count r, f32[n] master parameters,
+// f32[n] Adam first moments, f32[n] second moments, r caller-state bytes, u32 CRC-32 of every
+// byte before it.
+namespace {
+
+constexpr unsigned char kCkptMagic[8] = {'P', 'D', 'C', 'N', 'N', 'C', 'K', 0};
+constexpr uint32_t kCkptVersion = 1;
+constexpr size_t kCkptHeader = 32;
+constexpr size_t kCkptMaxState = (size_t)1 << 20;
+
+// CRC-32 of the IEEE 802.3 / zlib convention: reflected polynomial 0xEDB88320, initial value and
+// final xor 0xFFFFFFFF, table-driven one byte at a time.
+uint32_t crc32_ieee(const unsigned char* p, size_t n) {
+  static const std::vector<uint32_t> table = [] {
+    std::vector<uint32_t> t(256);
+    for (uint32_t i = 0; i < 256; ++i) {
+      uint32_t c = i;
+      for (int k = 0; k < 8; ++k) c = (c & 1u) ? 0xEDB88320u ^ (c >> 1) : c >> 1;
+      t[i] = c;
+    }
+    return t;
+  }();
+  uint32_t c = 0xFFFFFFFFu;
+  for (size_t i = 0; i < n; ++i) c = table[(c ^ p[i]) & 0xffu] ^ (c >> 8);
+  return c ^ 0xFFFFFFFFu;
+}
+
+void put_u32(std::vector<unsigned char>& b, uint32_t v) {
+  for (int i = 0; i < 4; ++i) b.push_back((unsigned char)(v >> (8 * i)));
+}
+void put_u64(std::vector<unsigned char>& b, uint64_t v) {
+  for (int i = 0; i < 8; ++i) b.push_back((unsigned char)(v >> (8 * i)));
+}
+uint32_t get_u32(const unsigned char* p) {
+  uint32_t v = 0;
+  for (int i = 0; i < 4; ++i) v |= (uint32_t)p[i] << (8 * i);
+  return v;
+}
+uint64_t get_u64(const unsigned char* p) {
+  uint64_t v = 0;
+  for (int i = 0; i < 8; ++i) v |= (uint64_t)p[i] << (8 * i);
+  return v;
+}
+void put_f32s(std::vector<unsigned char>& b, const std::vector<float>& x) {
+  for (float f : x) {
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    put_u32(b, u);
+  }
+}
+void get_f32s(const unsigned char* p, size_t n, std::vector<float>& x) {
+  x.resize(n);
+  for (size_t i = 0; i < n; ++i) {
+    const uint32_t u = get_u32(p + 4 * i);
+    memcpy(&x[i], &u, 4);
+  }
+}
+
+struct Ckpt {
+  uint32_t version = 0, n = 0;
+  uint64_t step = 0, state_bytes = 0;
+  const unsigned char* theta = nullptr;  // views into the file bytes
+  const unsigned char* state = nullptr;
+};
+
+// Reads and checks a checkpoint file; on success `buf` holds it and `out` points into it.
+bool read_ckpt(const char* path, std::vector<unsigned char>& buf, Ckpt& out, std::string& why) {
+  FILE* f = fopen(path, "rb");
+  if (!f) {
+    why = "cannot open the file";
+    return false;
+  }
+  buf.clear();
+  unsigned char tmp[65536];
+  size_t got;
+  while ((got = fread(tmp, 1, sizeof(tmp), f)) > 0) {
+    buf.insert(buf.end(), tmp, tmp + got);
+    if (buf.size() > ((size_t)256 << 20)) break;
+  }
+  const bool err = ferror(f) != 0;
+  fclose(f);
+  if (err) {
+    why = "read error";
+    return false;
+  }
+  if (buf.size() < kCkptHeader + 4 || memcmp(buf.data(), kCkptMagic, 8) != 0) {
+    why = "not a band-network checkpoint (magic)";
+    return false;
+  }
+  out.version = get_u32(buf.data() + 8);
+  out.n = get_u32(buf.data() + 12);
+  out.step = get_u64(buf.data() + 16);
+  out.state_bytes = get_u64(buf.data() + 24);
+  if (out.version != kCkptVersion) {
+    why = "unknown format version";
+    return false;
+  }
+  if (out.state_bytes > kCkptMaxState || out.n > (1u << 24)) {
+    why = "size fields out of range";
+    return false;
+  }
+  const size_t want = kCkptHeader + (size_t)12 * out.n + (size_t)out.state_bytes + 4;
+  if (buf.size() != want) {
+    why = "file size does not match its header";
+    return false;
+  }
+  if (crc32_ieee(buf.data(), want - 4) != get_u32(buf.data() + want - 4)) {
+    why = "CRC-32 mismatch";
+    return false;
+  }
+  out.theta = buf.data() + kCkptHeader;
+  out.state = buf.data() + kCkptHeader + (size_t)12 * out.n;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+pd_status pd_cnn_checkpoint_info(const char* path, int* n_params, long long* step,
+                                 size_t* state_bytes) {
+  if (!path) return PD_ERR_INVALID_ARG;
+  std::vector<unsigned char> buf;
+  Ckpt c;
+  std::string why;
+  if (!read_ckpt(path, buf, c, why)) return PD_ERR_INVALID_ARG;
+  if (n_params) *n_params = (int)c.n;
+  if (step) *step = (long long)c.step;
+  if (state_bytes) *state_bytes = (size_t)c.state_bytes;
+  return PD_OK;
+}
+
+pd_status pd_cnn_save(pd_ctx* ctx, pd_cnn* net, const char* path, const void* state,
+                      size_t state_bytes) {
+  if (!ctx) return PD_ERR_INVALID_ARG;
+  if (!net || !path) return fail(ctx, PD_ERR_INVALID_ARG, "NULL network or path");
+  if (state_bytes > kCkptMaxState || (state_bytes && !state))
+    return fail(ctx, PD_ERR_INVALID_ARG, "caller state of %zu bytes (at most %zu, non-NULL)",
+                state_bytes, kCkptMaxState);
+  pd_status st = cuda_ok(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (st != PD_OK) return st;
+  const size_t n = (size_t)net->desc.n_params;
+  std::vector<float> th(n), m(n), v(n);
+  cudaStream_t s = ctx->stream;
+  st = cuda_ok(ctx, cudaMemcpyAsync(th.data(), net->theta, n * 4, cudaMemcpyDeviceToHost, s),
+               "checkpoint download");
+  if (st == PD_OK)
+    st = cuda_ok(ctx, cudaMemcpyAsync(m.data(), net->adam_m, n * 4, cudaMemcpyDeviceToHost, s),
+                 "checkpoint download");
+  if (st == PD_OK)
+    st = cuda_ok(ctx, cudaMemcpyAsync(v.data(), net->adam_v, n * 4, cudaMemcpyDeviceToHost, s),
+                 "checkpoint download");
+  if (st == PD_OK) st = cuda_ok(ctx, cudaStreamSynchronize(s), "pd_cnn_save");
+  if (st != PD_OK) return st;
+  std::vector<unsigned char> b;
+  b.reserve(kCkptHeader + 12 * n + state_bytes + 4);
+  b.insert(b.end(), kCkptMagic, kCkptMagic + 8);
+  put_u32(b, kCkptVersion);
+  put_u32(b, (uint32_t)n);
+  put_u64(b, (uint64_t)net->step);
+  put_u64(b, (uint64_t)state_bytes);
+  put_f32s(b, th);
+  put_f32s(b, m);
+  put_f32s(b, v);
+  const unsigned char* sp = static_cast<const unsigned char*>(state);
+  if (state_bytes) b.insert(b.end(), sp, sp + state_bytes);
+  put_u32(b, crc32_ieee(b.data(), b.size()));
+  // written whole to a temporary file, then renamed over the target
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = fopen(tmp.c_str(), "wb");
+  if (!f) return fail(ctx, PD_ERR_INVALID_ARG, "cannot create %s", tmp.c_str());
+  const bool ok = fwrite(b.data(), 1, b.size(), f) == b.size();
+  const bool closed = fclose(f) == 0;
+  if (!ok || !closed || rename(tmp.c_str(), path) != 0) {
+    remove(tmp.c_str());
+    return fail(ctx, PD_ERR_INVALID_ARG, "cannot write %s", path);
+  }
+  return PD_OK;
+}
+
+pd_status pd_cnn_load(pd_ctx* ctx, pd_cnn* net, const char* path, void* state, size_t state_cap,
+                      size_t* state_bytes) {
+  if (!ctx) return PD_ERR_INVALID_ARG;
+  if (!net || !path) return fail(ctx, PD_ERR_INVALID_ARG, "NULL network or path");
+  std::vector<unsigned char> buf;
+  Ckpt c;
+  std::string why;
+  if (!read_ckpt(path, buf, c, why))
+    return fail(ctx, PD_ERR_INVALID_ARG, "%s: %s", path, why.c_str());
+  if ((int)c.n != net->desc.n_params)
+    return fail(ctx, PD_ERR_INVALID_ARG, "%s holds %u parameters, the network has %d", path, c.n,
+                net->desc.n_params);
+  pd_status st = cuda_ok(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (st != PD_OK) return st;
+  const size_t n = c.n;
+  std::vector<float> th, m, v;
+  get_f32s(c.theta, n, th);
+  get_f32s(c.theta + 4 * n, n, m);
+  get_f32s(c.theta + 8 * n, n, v);
+  cudaStream_t s = ctx->stream;
+  st = cuda_ok(ctx, cudaMemcpyAsync(net->theta, th.data(), n * 4, cudaMemcpyHostToDevice, s),
+               "checkpoint upload");
+  if (st == PD_OK)
+    st = cuda_ok(ctx, cudaMemcpyAsync(net->adam_m, m.data(), n * 4, cudaMemcpyHostToDevice, s),
+                 "checkpoint upload");
+  if (st == PD_OK)
+    st = cuda_ok(ctx, cudaMemcpyAsync(net->adam_v, v.data(), n * 4, cudaMemcpyHostToDevice, s),
+                 "checkpoint upload");
+  if (st != PD_OK) return st;
+  net->step = (int)c.step;
+  refresh_weights(s, net, 0, 0.0f, nullptr);
+  // the host vectors must stay valid until the copies have run
+  st = cuda_ok(ctx, cudaStreamSynchronize(s), "pd_cnn_load");
+  if (st != PD_OK) return st;
+  if (state && state_cap) memcpy(state, c.state, std::min(state_cap, (size_t)c.state_bytes));
+  if (state_bytes) *state_bytes = (size_t)c.state_bytes;
+  return PD_OK;
+}
 
 pd_status pd_cnn_set_params(pd_ctx* ctx, pd_cnn* net, const float* host_params, int n) {
   if (!ctx || !net || !host_params) return fail(ctx, PD_ERR_INVALID_ARG, "NULL argument");

@@ -277,3 +277,63 @@ def test_learned_path_is_the_composition(B, ctx):
     assert torch.equal(tl, tl2) and torch.equal(d, d2) and torch.equal(D1, D12)
     assert (tl >= 0).float().mean().item() > 0.5
     net.close()
+
+
+def _train(B, ctx, net, xs, ts, lr, first, stop):
+    for i in range(first, stop):
+        B.pd_cnn_train_step(ctx, net, xs[i], ts[i], lr)
+    torch.cuda.synchronize()
+
+
+def test_training_is_bit_reproducible_and_resumes_from_a_checkpoint(B, ctx, tmp_path):
+    """The gradient sums run in a fixed order, so two runs of the same 5 Adam steps give the same
+    bits; a run of 2 steps saved to a checkpoint, loaded into a fresh network and trained 3 more
+    steps gives those bits too (parameters, both Adam moments and the step count: the two final
+    checkpoint files are byte-identical), and the caller state saved with it comes back."""
+    th = _theta(31)
+    Bn, Hd, Wd = 3, 37, 53
+    Ho, Wo = (Hd + 3) // 4, (Wd + 3) // 4
+    xs = [_to_dev_bf16(_input(40 + i, Bn, Hd, Wd)) for i in range(5)]
+    ts = [torch.from_numpy(_targets(50 + i, Bn, Ho, Wo)).cuda() for i in range(5)]
+    lr = 1e-3
+    state = bytes(range(256)) * 3 + b"generator"
+
+    def fresh():
+        n = B.Cnn(0, max_batch=Bn, max_hd=Hd, max_wd=Wd)
+        B.pd_cnn_set_params(ctx, n, th)
+        return n
+
+    a, b = fresh(), fresh()
+    _train(B, ctx, a, xs, ts, lr, 0, 5)
+    _train(B, ctx, b, xs, ts, lr, 0, 5)
+    pa = B.pd_cnn_get_params(ctx, a)
+    assert np.array_equal(pa.view(np.uint32), B.pd_cnn_get_params(ctx, b).view(np.uint32))
+    assert not np.array_equal(pa, th)                      # the steps did move the parameters
+
+    c = fresh()
+    _train(B, ctx, c, xs, ts, lr, 0, 2)
+    mid = str(tmp_path / "mid.ckpt")
+    B.pd_cnn_save(ctx, c, mid, state)
+    assert B.pd_cnn_checkpoint_info(mid) == {"n_params": B.pd_cnn_num_params(), "step": 2,
+                                             "state_bytes": len(state)}
+    d = B.Cnn(0, max_batch=Bn, max_hd=Hd, max_wd=Wd)       # zero parameters, no Adam state
+    assert B.pd_cnn_load(ctx, d, mid) == state
+    _train(B, ctx, d, xs, ts, lr, 2, 5)
+    B.pd_cnn_check(ctx, d)
+    assert np.array_equal(pa.view(np.uint32), B.pd_cnn_get_params(ctx, d).view(np.uint32))
+    fa, fd = str(tmp_path / "a.ckpt"), str(tmp_path / "d.ckpt")
+    B.pd_cnn_save(ctx, a, fa, state)
+    B.pd_cnn_save(ctx, d, fd, state)
+    assert open(fa, "rb").read() == open(fd, "rb").read()
+
+    # a damaged file is refused and leaves the network as it was
+    raw = bytearray(open(mid, "rb").read())
+    raw[100] ^= 0x01
+    bad = str(tmp_path / "bad.ckpt")
+    open(bad, "wb").write(bytes(raw))
+    with pytest.raises(B.PdError) as e:
+        B.pd_cnn_load(ctx, d, bad)
+    assert e.value.status == B.PD_ERR_INVALID_ARG
+    assert np.array_equal(pa.view(np.uint32), B.pd_cnn_get_params(ctx, d).view(np.uint32))
+    for n in (a, b, c, d):
+        n.close()
