@@ -455,9 +455,9 @@ extern "C" pd_status pd_sgm_batch(pd_ctx* ctx, const pd_pair* pairs, int n, cons
       int cnt[kBatchStages];
       batch_stage_blocks(q.W, q.H, q.D, cnt);
       for (int k = 0; k < kBatchStages; ++k) starts[k][j + 1] = starts[k][j] + cnt[k];
-      const int lpw = batch_lines_per_warp(q.D);
       for (int r = 0; r < p->paths; ++r) {
         const int dx = kDx[r], dy = kDy[r];
+        const int lpw = batch_lines_per_warp(q.D, dx, dy);
         const int nlines = dy == 0 ? q.H : (dx == 0 ? q.W : q.W + q.H - 1);
         const int nsteps = dy == 0 ? q.W : (dx == 0 ? q.H : std::min(q.W, q.H));
         Seg sg;

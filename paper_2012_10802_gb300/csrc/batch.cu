@@ -70,14 +70,31 @@ __global__ void k_fill_b(const BatchPair* __restrict__ pairs, const int* __restr
     p.rkeys[k] = 0xffffffffu;
 }
 
+// The walk of one task: rows with GH = D/16 lanes of one 16-disparity group each, columns and
+// diagonals with GO = D/32 lanes of two groups each (as the single-pair aggregation).
+template <int GH, int GO>
+__device__ __forceinline__ void batch_walk(const BatchPair& p, uint8_t* dst, int dx, int dy,
+                                           int local, uint32_t P1x2, uint32_t K21x2,
+                                           uint4* ring) {
+  if (dy == 0)
+    agg_walk<GH, 1, true>(p.cost, dst, p.W, p.H, p.D, dx, 0, P1x2, K21x2, local * (32 / GH), ring);
+  else if (dx == 0)
+    agg_walk<GO, 2, true>(p.cost, dst, p.W, p.H, p.D, 0, dy, P1x2, K21x2, local * (32 / GO), ring);
+  else
+    agg_walk<GO, 2, false>(p.cost, dst, p.W, p.H, p.D, dx, dy, P1x2, K21x2, local * (32 / GO),
+                           ring);
+}
+
 // Persistent aggregation.  Task t belongs to the segment s with seg[s].first <= t; its lines are
-// first = (t - seg[s].first) * 32 / G onwards.
+// (t - seg[s].first) * (lines per warp of the segment's direction) onwards.
 __global__ void __launch_bounds__(256) k_aggregate_b(const BatchPair* __restrict__ pairs,
                                                      const BatchSegment* __restrict__ seg,
                                                      int nseg, int ntasks,
                                                      unsigned int* __restrict__ counter,
                                                      uint32_t P1x2, uint32_t K21x2) {
+  extern __shared__ uint4 s_ring[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint4* ring = s_ring + (size_t)warp * kStages * 32;  // 8 KB per warp
   for (;;) {
     unsigned int t = 0;
     if (lane == 0) t = atomicAdd(counter, 1u);
@@ -93,14 +110,13 @@ __global__ void __launch_bounds__(256) k_aggregate_b(const BatchPair* __restrict
     }
     const BatchSegment sg = seg[lo];
     const BatchPair& p = pairs[sg.pair];
-    const int dx = sg.dx, dy = sg.dy;
     uint8_t* dst = p.vols + (size_t)sg.r * p.vol_bytes;
     const int local = (int)t - sg.first;
     switch (p.D) {
-      case 32: agg_warp<2>(p.cost, dst, p.W, p.H, p.D, dx, dy, P1x2, K21x2, local * 16, warp); break;
-      case 64: agg_warp<4>(p.cost, dst, p.W, p.H, p.D, dx, dy, P1x2, K21x2, local * 8, warp); break;
-      case 128: agg_warp<8>(p.cost, dst, p.W, p.H, p.D, dx, dy, P1x2, K21x2, local * 4, warp); break;
-      default: agg_warp<16>(p.cost, dst, p.W, p.H, p.D, dx, dy, P1x2, K21x2, local * 2, warp); break;
+      case 32: batch_walk<2, 1>(p, dst, sg.dx, sg.dy, local, P1x2, K21x2, ring); break;
+      case 64: batch_walk<4, 2>(p, dst, sg.dx, sg.dy, local, P1x2, K21x2, ring); break;
+      case 128: batch_walk<8, 4>(p, dst, sg.dx, sg.dy, local, P1x2, K21x2, ring); break;
+      default: batch_walk<16, 8>(p, dst, sg.dx, sg.dy, local, P1x2, K21x2, ring); break;
     }
   }
 }
@@ -140,7 +156,9 @@ void batch_stage_blocks(int W, int H, int D, int counts[kBatchStages]) {
   counts[kStageLr] = ((W + 255) / 256) * H;
 }
 
-int batch_lines_per_warp(int D) { return 32 / (D / 16); }
+int batch_lines_per_warp(int D, int dx, int dy) {
+  return dy == 0 ? 32 / (D / 16) : 32 / (D / 32);  // rows: one group per lane; others: two
+}
 
 size_t batch_agg_smem(int warps_per_block) {
   return (size_t)warps_per_block * kStages * 32 * sizeof(uint4);

@@ -25,7 +25,7 @@ struct BatchPair {
 };
 
 // A run of aggregation tasks: direction r = (dx, dy) of one pair; task `first` + j covers the
-// j-th group of 32 / G lines.
+// j-th group of batch_lines_per_warp(D, dx, dy) lines.
 struct BatchSegment {
   int first, pair, r, dx, dy, pad;
 };
@@ -43,7 +43,8 @@ struct BatchWaveDev {
 };
 
 void batch_stage_blocks(int W, int H, int D, int counts[kBatchStages]);
-int batch_lines_per_warp(int D);
+// lines a warp walks in one aggregation task of direction (dx, dy)
+int batch_lines_per_warp(int D, int dx, int dy);
 size_t batch_agg_smem(int warps_per_block);
 int batch_max_blocks_per_sm(int agg_warps);
 void launch_batch_wave(cudaStream_t s, const BatchWaveDev& w, int P1, int P2, int lr_tol,

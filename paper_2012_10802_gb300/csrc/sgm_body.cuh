@@ -275,116 +275,12 @@ __device__ __forceinline__ uint32_t group_in_mask(int g, int lo, int hi) {
 }
 
 // The lines first .. first + 32/G - 1 of direction (dx, dy), walked by the calling warp (all 32
-// lanes call it; `warp` selects the warp's part of the block's cost ring).  L goes to dst_vol.
-template <int G>
-__device__ __forceinline__ void agg_warp(const uint8_t* __restrict__ cost,
-                                         uint8_t* __restrict__ dst_vol, int W, int H, int D,
-                                         int dx, int dy, uint32_t P1x2, uint32_t K21x2, int first,
-                                         int warp) {
-  constexpr int LPW = 32 / G;  // lines per warp
-  const int nlines = dy == 0 ? H : (dx == 0 ? W : W + H - 1);
-  const int lane = threadIdx.x & 31;
-  const int g = lane % G;
-  if (first >= nlines) return;  // the whole warp leaves together
-  const int line = first + lane / G;
-  const int last = min(first + LPW, nlines) - 1;
-  const LineWalk lw = line_walk(dx, dy, W, H, D, line, first, last, line < nlines);
-  const uint8_t* csrc = cost + 16 * g;
-  uint8_t* dst = dst_vol + 16 * g;
-
-  // State: L of the previous pixel on the line (the oracle's normalised value) and its minimum
-  // mp over all disparities, replicated in both u16 halves.  A line starts from L = 0, mp = 0,
-  // which makes its first pixel's L equal to the cost.
-  uint32_t N[8];
-#pragma unroll
-  for (int j = 0; j < 8; ++j) N[j] = 0;
-  uint32_t mp = 0;
-
-  // Cost rows arrive through a per-warp ring in shared memory: stage k of lane `lane` holds the
-  // 16 cost bytes of one step.  Step s is read from stage s % kStages after waiting for its copy;
-  // the copy for step s + kStages - 1 then goes into the stage read one step earlier.
-  extern __shared__ uint4 s_ring[];
-  uint4* ring = s_ring + (size_t)warp * kStages * 32 + lane;
-  const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
-  long long pf_off = lw.off0;  // offset of the step being prefetched
-#pragma unroll
-  for (int k = 0; k < kStages - 1; ++k) {
-    const bool in = k >= lw.s_first && k <= lw.s_last;
-    cp_async16(ring_s + k * 32 * 16, csrc + (in ? pf_off : 0), in ? 16u : 0u);
-    cp_async_commit();
-    pf_off += lw.delta;
-  }
-  long long st_off = lw.off0;  // offset of the current step
-  for (int s0 = 0; s0 < lw.nsteps; s0 += kStages) {
-#pragma unroll
-    for (int k = 0; k < kStages; ++k) {
-      const int s = s0 + k;
-      if (s >= lw.nsteps) break;  // warp-uniform
-      const bool act = s >= lw.s_first && s <= lw.s_last;
-      cp_async_wait<kStages - 2>();  // the copy of step s is complete
-      const uint4 rv = ring[k * 32];
-      const uint32_t raw[4] = {rv.x, rv.y, rv.z, rv.w};
-      {
-        const int sp = s + kStages - 1;
-        const bool in = sp >= lw.s_first && sp <= lw.s_last;
-        cp_async16(ring_s + ((k + kStages - 1) % kStages) * 32 * 16, csrc + (in ? pf_off : 0),
-                   in ? 16u : 0u);
-        cp_async_commit();
-        pf_off += lw.delta;
-      }
-      // neighbours across the lane boundaries of this line's lane group
-      uint32_t prevHi = kBig2, nextLo = kBig2;
-      if constexpr (G > 1) {
-        uint32_t up = __shfl_up_sync(kFull, N[7], 1, G);
-        uint32_t dn = __shfl_down_sync(kFull, N[0], 1, G);
-        if (g > 0) prevHi = up;
-        if (g < G - 1) nextLo = dn;
-      }
-      const uint32_t left0 = __byte_perm(prevHi, N[7], 0x5432);
-      const uint32_t right7 = __byte_perm(N[0], nextLo, 0x5432);
-      const uint32_t K = mp + K21x2;  // m + P2 - P1 in both halves (no carry: all < 2^15)
-      uint32_t Lw[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        uint32_t lft = j == 0 ? left0 : N[j - 1];
-        uint32_t rgt = j == 7 ? right7 : N[j + 1];
-        // min(L[d-1], L[d+1], m + P2 - P1) + P1 against L[d]: the minimum of Eq. (8)
-        uint32_t t = __vimin3_u16x2(lft, rgt, K);
-        t = __viaddmin_u16x2(t, P1x2, N[j]);
-        uint32_t c = __byte_perm(raw[j >> 1], 0, (j & 1) ? 0x4342 : 0x4140);
-        // c + t - m in one 32-bit three-input add: each half of t is >= m, so no borrow or
-        // carry crosses between the halves
-        Lw[j] = t + c - mp;
-      }
-      uint32_t m = __vimin3_u16x2(__vimin3_u16x2(Lw[0], Lw[1], Lw[2]),
-                                  __vimin3_u16x2(Lw[3], Lw[4], Lw[5]), __vminu2(Lw[6], Lw[7]));
-      m = __vminu2(m, __byte_perm(m, m, 0x1032));  // both halves = min of the two halves
-#pragma unroll
-      for (int o = 1; o < G; o <<= 1) m = __vminu2(m, __shfl_xor_sync(kFull, m, o, G));
-      if (act) {
-        uint4 w;
-        w.x = __byte_perm(Lw[0], Lw[1], 0x6420);
-        w.y = __byte_perm(Lw[2], Lw[3], 0x6420);
-        w.z = __byte_perm(Lw[4], Lw[5], 0x6420);
-        w.w = __byte_perm(Lw[6], Lw[7], 0x6420);
-        __stcs(reinterpret_cast<uint4*>(dst + st_off), w);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) N[j] = Lw[j];
-        mp = m;
-      } else {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) N[j] = 0;
-        mp = 0;
-      }
-      st_off += lw.delta;
-    }
-  }
-  cp_async_wait<0>();  // no copy may still be in flight when the warp exits
-}
-
-// The walker of the persistent aggregation: like agg_warp, for lines of G lanes that each keep NG
-// consecutive 16-disparity groups (G * NG = D / 16; NG = 1 or 2), with the warp's ring passed in
-// (ring_base: ST = 16 / NG stages of 32 lanes x NG x 16 bytes, 8 KB).  With two groups a lane
+// lanes call it) with G lanes per line that each keep NG consecutive 16-disparity groups
+// (G * NG = D / 16; NG = 1 or 2).  State: L of the previous pixel on the line (the oracle's
+// normalised value) and its minimum over all disparities, replicated in both u16 halves; a line
+// starts from L = 0, m = 0, which makes its first pixel's L equal to the cost.  Costs arrive
+// through the warp's ring in shared memory (ring_base: ST = 16 / NG stages of 32 lanes x NG x 16
+// bytes, 8 KB), ST - 1 steps ahead; L leaves with streaming 16-byte stores to dst_vol.  With two groups a lane
 // carries 16 words: the step between its groups is a byte permutation inside the lane, so a line
 // needs half the lanes, shuffles and per-step bookkeeping of one group per lane.  FULL: every
 // line of the warp lies inside the image at every step (rows and columns), so a lane is active
