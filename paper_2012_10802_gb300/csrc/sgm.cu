@@ -115,9 +115,11 @@ constexpr int kAggPWarps = 4;               // warps per block of the persistent
 constexpr int kAggPRingUint4 = 512;         // 8 KB ring per warp
 
 // Persistent aggregation of Eq. (8) over all directions of a frame.  Each warp repeatedly takes
-// the next task from the counter; rows are walked with GH = D/16 lanes of one 16-disparity group
-// each, columns and diagonals with GO = D/32 lanes of two groups each.
-template <int GH, int GO>
+// the next task from the counter; columns and diagonals are walked with GO = D/32 lanes of two
+// 16-disparity groups each; rows with GH lanes, of one group each (D/16 lanes), or of half a group
+// each when HALF (D/8 lanes, used at D = 32, where it measured faster; at D = 128 it measured
+// slower).
+template <int GH, int GO, bool HALF>
 __global__ void __launch_bounds__(kAggPWarps * 32) k_aggregate_p(
     const uint8_t* __restrict__ cost, uint8_t* __restrict__ out, int W, int H, int D,
     AggPlan plan, uint32_t P1x2, uint32_t K21x2, size_t vol_bytes,
@@ -153,8 +155,12 @@ __global__ void __launch_bounds__(kAggPWarps * 32) k_aggregate_p(
     }
     uint8_t* dst = out + (size_t)(code & 7u) * vol_bytes;
     const int dx = (int)((code >> 3) & 3u) - 1, dy = (int)((code >> 5) & 3u) - 1;
-    if (cls == 0)
-      agg_walk<GH, 1, true>(cost, dst, W, H, D, dx, 0, P1x2, K21x2, k * (32 / GH), ring);
+    if (cls == 0) {
+      if constexpr (HALF)
+        agg_row_half<GH>(cost, dst, W, H, D, dx, P1x2, K21x2, k * (32 / GH), ring);
+      else
+        agg_walk<GH, 1, true>(cost, dst, W, H, D, dx, 0, P1x2, K21x2, k * (32 / GH), ring);
+    }
     else if (cls == 1)
       agg_walk<GO, 2, true>(cost, dst, W, H, D, 0, dy, P1x2, K21x2, k * (32 / GO), ring);
     else
@@ -333,12 +339,12 @@ void launch_to_natural(cudaStream_t s, const uint8_t* inter, size_t n_pix, int D
 }
 
 namespace {
-template <int GH, int GO>
+template <int GH, int GO, bool HALF>
 void launch_agg_p(cudaStream_t s, const uint8_t* cost, uint8_t* out, int W, int H, int D,
                   const AggPlan& plan, uint32_t P1x2, uint32_t K21x2, size_t vol_bytes,
                   unsigned int* counter) {
   const size_t smem = (size_t)kAggPWarps * kAggPRingUint4 * sizeof(uint4);
-  const void* f = (const void*)k_aggregate_p<GH, GO>;
+  const void* f = (const void*)k_aggregate_p<GH, GO, HALF>;
   raise_smem_limit(f, smem);
   // one wave of resident blocks: per device, the SM count times the blocks an SM holds
   static std::mutex mu;
@@ -352,7 +358,7 @@ void launch_agg_p(cudaStream_t s, const uint8_t* cost, uint8_t* out, int W, int 
     if (it == blocks.end()) {
       int sms = 0, per = 0;
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_aggregate_p<GH, GO>,
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_aggregate_p<GH, GO, HALF>,
                                                     kAggPWarps * 32, smem);
       nb = std::max(1, sms * std::max(1, per));
       blocks[dev] = nb;
@@ -362,7 +368,7 @@ void launch_agg_p(cudaStream_t s, const uint8_t* cost, uint8_t* out, int W, int 
   }
   nb = std::min(nb, (plan.ntasks + kAggPWarps - 1) / kAggPWarps);
   cudaMemsetAsync(counter, 0, sizeof(unsigned int), s);
-  k_aggregate_p<GH, GO><<<nb, kAggPWarps * 32, smem, s>>>(cost, out, W, H, D, plan, P1x2,
+  k_aggregate_p<GH, GO, HALF><<<nb, kAggPWarps * 32, smem, s>>>(cost, out, W, H, D, plan, P1x2,
                                                              K21x2, vol_bytes, counter);
 }
 }  // namespace
@@ -372,7 +378,7 @@ void launch_aggregate_p(cudaStream_t s, const uint8_t* cost_il, int W, int H, in
                         unsigned int* counter) {
   AggPlan plan;
   memset(&plan, 0, sizeof(plan));
-  const int GH = D / 16, GO = D / 32;
+  const int GH = D == 32 ? D / 8 : D / 16, GO = D / 32;
   const int lh = 32 / GH, lo = 32 / GO;
   plan.n_h = (H + lh - 1) / lh;
   plan.n_v = (W + lo - 1) / lo;
@@ -394,10 +400,10 @@ void launch_aggregate_p(cudaStream_t s, const uint8_t* cost_il, int W, int H, in
   const uint32_t P1x2 = (uint32_t)P1 * 0x10001u;
   const uint32_t K21x2 = (uint32_t)(P2 - P1) * 0x10001u;
   switch (D) {
-    case 32: launch_agg_p<2, 1>(s, cost_il, out, W, H, D, plan, P1x2, K21x2, vol_bytes, counter); break;
-    case 64: launch_agg_p<4, 2>(s, cost_il, out, W, H, D, plan, P1x2, K21x2, vol_bytes, counter); break;
-    case 128: launch_agg_p<8, 4>(s, cost_il, out, W, H, D, plan, P1x2, K21x2, vol_bytes, counter); break;
-    case 256: launch_agg_p<16, 8>(s, cost_il, out, W, H, D, plan, P1x2, K21x2, vol_bytes, counter); break;
+    case 32: launch_agg_p<4, 1, true>(s, cost_il, out, W, H, D, plan, P1x2, K21x2, vol_bytes, counter); break;
+    case 64: launch_agg_p<4, 2, false>(s, cost_il, out, W, H, D, plan, P1x2, K21x2, vol_bytes, counter); break;
+    case 128: launch_agg_p<8, 4, false>(s, cost_il, out, W, H, D, plan, P1x2, K21x2, vol_bytes, counter); break;
+    case 256: launch_agg_p<16, 8, false>(s, cost_il, out, W, H, D, plan, P1x2, K21x2, vol_bytes, counter); break;
     default: break;  // the API admits D in {32, 64, 128, 256} only
   }
 }

@@ -196,6 +196,12 @@ __device__ __forceinline__ void cp_async16(uint32_t smem, const void* gmem, uint
                "r"(src_bytes)
                : "memory");
 }
+// The same copy of 8 bytes (cp.async.ca: 4, 8 or 16 bytes); src_bytes = 0 writes zeros.
+__device__ __forceinline__ void cp_async8(uint32_t smem, const void* gmem, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(smem), "l"(gmem),
+               "r"(src_bytes)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -439,6 +445,95 @@ __device__ __forceinline__ void agg_walk(const uint8_t* __restrict__ cost,
 #pragma unroll 2
   for (; s <= s_all_hi && s < lw.nsteps; ++s) step(s, std::true_type{});
   for (; s < lw.nsteps; ++s) step(s, std::false_type{});
+  cp_async_wait<0>();  // no copy may still be in flight when the walk ends
+}
+
+// The rows (directions (+-1, 0), every line inside the image at every step) walked with G = D/8
+// lanes per row that each keep half a 16-disparity group: lane h holds words 4c .. 4c + 3 of
+// group h / 2 (c = h % 2), i.e. 8 disparities.  A row's step is then about half the instructions
+// of agg_walk's one group per lane, at one more shuffle level for the minimum.  Costs arrive 8
+// bytes per lane and step through the warp's ring (32 stages of 32 x 8 bytes, 8 KB); L leaves
+// with streaming 8-byte stores.
+template <int G>
+__device__ __forceinline__ void agg_row_half(const uint8_t* __restrict__ cost,
+                                             uint8_t* __restrict__ dst_vol, int W, int H, int D,
+                                             int dx, uint32_t P1x2, uint32_t K21x2, int first,
+                                             uint4* __restrict__ ring_base) {
+  constexpr int LPW = 32 / G;  // rows per warp
+  constexpr int ST = 32;       // ring stages
+  const int lane = threadIdx.x & 31;
+  const int h = lane % G, c = h & 1;
+  if (first >= H) return;  // the whole warp leaves together
+  const int line = first + lane / G;
+  const bool lvalid = line < H;
+  const LineWalk lw = line_walk(dx, 0, W, H, D, line, first, min(first + LPW, H) - 1, lvalid);
+  const uint8_t* csrc = cost + 8 * h;  // this lane's 8 bytes of the pixel's D
+  uint8_t* dst = dst_vol + 8 * h;
+  uint32_t N[4] = {0, 0, 0, 0};
+  uint32_t mp = 0;
+  const uint32_t ring_s =
+      (uint32_t)__cvta_generic_to_shared(reinterpret_cast<uint8_t*>(ring_base) + 8 * lane);
+  const uint2* ring = reinterpret_cast<const uint2*>(ring_base) + lane;
+  long long pf_off = lw.off0;
+#pragma unroll
+  for (int k = 0; k < ST - 1; ++k) {
+    const bool in = lvalid && k < lw.nsteps;
+    cp_async8(ring_s + k * 32 * 8, csrc + (in ? pf_off : 0), in ? 8u : 0u);
+    cp_async_commit();
+    pf_off += lw.delta;
+  }
+  long long st_off = lw.off0;
+  const int src = c == 0 ? lane + 1 : lane - 1;  // the other half of the group
+#pragma unroll 2
+  for (int s = 0; s < lw.nsteps; ++s) {
+    const int k = s & (ST - 1);
+    cp_async_wait<ST - 2>();  // the copy of step s is complete
+    const uint2 rv = ring[k * 32];
+    {
+      const int sp = s + ST - 1;
+      const bool in = lvalid && sp < lw.nsteps;
+      cp_async8(ring_s + ((k + ST - 1) & (ST - 1)) * 32 * 8, csrc + (in ? pf_off : 0),
+                in ? 8u : 0u);
+      cp_async_commit();
+      pf_off += lw.delta;
+    }
+    // neighbours: the previous lane's last word, the next lane's first word and, across the
+    // group's two halves, the group's word 7 (for c = 0) or word 0 (for c = 1)
+    uint32_t A = __shfl_up_sync(kFull, N[3], 1, G);
+    uint32_t Bn = __shfl_down_sync(kFull, N[0], 1, G);
+    if (h == 0) A = kBig2;
+    if (h == G - 1) Bn = kBig2;
+    const uint32_t Y = __shfl_sync(kFull, c == 1 ? N[3] : N[0], src);
+    const uint32_t lft0 = c == 0 ? __byte_perm(A, Y, 0x5432) : A;
+    const uint32_t rgt3 = c == 1 ? __byte_perm(Y, Bn, 0x5432) : Bn;
+    const uint32_t K = mp + K21x2;
+    const uint32_t raw[2] = {rv.x, rv.y};
+    uint32_t Lw[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t lft = j == 0 ? lft0 : N[j > 0 ? j - 1 : 0];
+      const uint32_t rgt = j == 3 ? rgt3 : N[j < 3 ? j + 1 : 3];
+      uint32_t t = __vimin3_u16x2(lft, rgt, K);
+      t = __viaddmin_u16x2(t, P1x2, N[j]);
+      const uint32_t cw = __byte_perm(raw[j >> 1], 0, (j & 1) ? 0x4342 : 0x4140);
+      Lw[j] = t + cw - mp;
+    }
+    uint32_t m = __vminu2(__vimin3_u16x2(Lw[0], Lw[1], Lw[2]), Lw[3]);
+    m = __vminu2(m, __byte_perm(m, m, 0x1032));
+    if constexpr (G == 32) {
+      m = __reduce_min_sync(kFull, m);  // both halves equal: the u32 order is the u16 order
+    } else {
+#pragma unroll
+      for (int o = 1; o < G; o <<= 1) m = __vminu2(m, __shfl_xor_sync(kFull, m, o, G));
+    }
+    if (lvalid)
+      __stcs(reinterpret_cast<uint2*>(dst + st_off),
+             make_uint2(__byte_perm(Lw[0], Lw[1], 0x6420), __byte_perm(Lw[2], Lw[3], 0x6420)));
+#pragma unroll
+    for (int j = 0; j < 4; ++j) N[j] = Lw[j];
+    mp = m;
+    st_off += lw.delta;
+  }
   cp_async_wait<0>();  // no copy may still be in flight when the walk ends
 }
 
