@@ -278,7 +278,9 @@ pd_status pd_pothole_mask(pd_ctx* ctx, const float* D2, const float* D1, const f
 
 /* on != 0: later pd_sgm and pd_run_pipeline calls record CUDA events on the context's stream
  * around their stages (no synchronisation; at most 4096 calls are recorded between reads).
- * on == 0 stops recording and discards what was recorded. */
+ * on == 2 records only the two events around the aggregation (aggregate_ms and total_ms are then
+ * the aggregation's time): every event in the stream drains the GPU between two stages, so this
+ * mode disturbs a timed run least.  on == 0 stops recording and discards what was recorded. */
 pd_status pd_profile_enable(pd_ctx* ctx, int on);
 /* Waits for the recorded events, writes the summed stage times to *out (host) and starts a new
  * recording. */

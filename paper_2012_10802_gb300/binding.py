@@ -616,7 +616,8 @@ def road_model_tensor(ctx, model):
 
 
 def pd_profile_enable(ctx, on=True):
-    ctx.check(lib().pd_profile_enable(ctx.h, 1 if on else 0))
+    """on: True / 1 every stage's events, 2 only the two around the aggregation, False / 0 off."""
+    ctx.check(lib().pd_profile_enable(ctx.h, 2 if (on == 2 and on is not True) else (1 if on else 0)))
 
 
 def pd_pipeline_config(ctx, use_graph=True):

@@ -100,7 +100,7 @@ pd_prof_rec* prof_begin(pd_ctx* c) {
 }
 
 void mark(pd_ctx* c, pd_prof_rec* r, int i) {
-  if (!r) return;
+  if (!r || !(c->prof_mask >> i & 1)) return;
   if (r == &c->cap_rec) {  // capturing: an external event-record node, retargeted per replay
     cudaEventRecordWithFlags(c->cap_ev[i], c->stream, cudaEventRecordExternal);
     c->cap_used |= 1 << i;
@@ -1176,7 +1176,7 @@ pd_status pipeline_graph_run(pd_ctx* ctx, const uint8_t* left, const uint8_t* ri
   put(p, sizeof *p);
   put(out, sizeof *out);
   put(&ctx->ws, sizeof ctx->ws);
-  const int prof = ctx->prof ? 1 : 0;
+  const int prof = ctx->prof ? ctx->prof_mask : 0;
   put(&prof, sizeof prof);
   const auto* held = static_cast<const std::vector<unsigned char>*>(ctx->pipe_key);
   if (!ctx->pipe_exec || !held || *held != key)
@@ -1208,6 +1208,8 @@ pd_status pipeline_graph_run(pd_ctx* ctx, const uint8_t* left, const uint8_t* ri
 pd_status pd_profile_enable(pd_ctx* ctx, int on) {
   if (!ctx) return PD_ERR_INVALID_ARG;
   ctx->prof = on != 0;
+  // on == 2: only the two marks around the aggregation (after the prep, after the aggregation)
+  ctx->prof_mask = on == 2 ? 0x6 : 0x7f;
   ctx->nrec = 0;
   ctx->launches = 0;
   return PD_OK;
@@ -1221,13 +1223,16 @@ pd_status pd_profile_read(pd_ctx* ctx, pd_profile* out) {
                      &out->transform_ms, &out->superpixel_ms, &out->mask_ms};
   for (int i = 0; i < ctx->nrec; ++i) {
     pd_prof_rec& r = ctx->recs[i];
-    int last = -1;
+    int first = -1, last = -1;
     for (int k = 0; k < 7; ++k)
-      if (r.used & (1 << k)) last = k;
-    if (last < 1 || !(r.used & 1)) continue;
+      if (r.used & (1 << k)) {
+        if (first < 0) first = k;
+        last = k;
+      }
+    if (first < 0 || last <= first) continue;
     PD_TRY(cuda_ok(ctx, cudaEventSynchronize(r.ev[last]), "pd_profile_read"));
-    int prev = 0;
-    for (int k = 1; k <= last; ++k) {
+    int prev = first;
+    for (int k = first + 1; k <= last; ++k) {
       if (!(r.used & (1 << k))) continue;
       float ms = 0.f;
       cudaEventElapsedTime(&ms, r.ev[prev], r.ev[k]);
@@ -1235,7 +1240,7 @@ pd_status pd_profile_read(pd_ctx* ctx, pd_profile* out) {
       prev = k;
     }
     float tot = 0.f;
-    cudaEventElapsedTime(&tot, r.ev[0], r.ev[last]);
+    cudaEventElapsedTime(&tot, r.ev[first], r.ev[last]);
     out->total_ms += tot;
     out->calls += 1;
   }

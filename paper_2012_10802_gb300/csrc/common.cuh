@@ -33,6 +33,7 @@ struct pd_ctx {
   void* graph_sig = nullptr;  // std::vector<long long>* signature of the captured batch
   void* tuned = nullptr;      // std::map<signature, warps per block>*
   bool prof = false;
+  int prof_mask = 0x7f;  // the stage marks recorded while profiling (bit i: mark i)
   pd_prof_rec* recs = nullptr;  // kMaxProf records, events created on first use
   int nrec = 0;
   long long launches = 0;       // kernels launched by profiled calls
