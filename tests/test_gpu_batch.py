@@ -100,3 +100,34 @@ def test_batch_rejects_bad_pairs(B):
         B.pd_sgm_batch(ctx, batch, B.default_params())
     assert e.value.status == B.PD_ERR_INVALID_ARG
     ctx.close()
+
+
+@pytest.mark.slow
+def test_benchmark_batch_shapes_in_the_benchmark_configuration(B, orc):
+    """The first 16 pairs of the benchmark's mixed batch (resolutions from {640x480, 1280x720,
+    1920x1080}, D from {32, 64, 128}, rolls in +-3 deg), run as the benchmark runs them (CUDA
+    graph, autotuned block shape, a second replay): every output equals the single-pair call's,
+    and a 1920x1080 pair's row shifts, disparities and D1 equal the oracle's."""
+    ctx = B.Context(0)
+    B.pd_batch_config(ctx, use_graph=True, autotune=True)
+    scenes = synth.mixed_batch(16)
+    assert {(sc.W, sc.H) for sc, _ in scenes} == {(640, 480), (1280, 720), (1920, 1080)}
+    items = []
+    for sc, D in scenes:
+        left, right = synth.render(sc)
+        items.append((torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda(),
+                      B.RoadModel.make(*synth.true_model(sc)), D, sc))
+    batch = B.make_batch(ctx, [it[:4] for it in items])
+    for _ in range(3):          # autotune, capture, replay
+        B.pd_sgm_batch(ctx, batch, B.default_params())
+    torch.cuda.synchronize()
+    _check_against_single(B, ctx, items, batch[1], 8)
+    k = next(i for i, (sc, _) in enumerate(scenes) if (sc.W, sc.H) == (1920, 1080))
+    sc, D = scenes[k]
+    left, right = (t.cpu().numpy() for t in items[k][:2])
+    ref = orc.sgm(left, right, orc.RoadModel.make(*synth.true_model(sc)), orc.Params(D=D, paths=8))
+    o = batch[1][k]
+    assert np.array_equal(o["kappa"].cpu().numpy(), ref["kappa"])
+    assert np.array_equal(o["d_int"].cpu().numpy(), ref["d_int"])
+    assert np.array_equal(o["D1"].cpu().numpy(), ref["D1"])
+    ctx.close()
