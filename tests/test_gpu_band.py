@@ -89,6 +89,27 @@ def test_band_matches_oracle(B, ctx, orc, W, H, D, paths, kind):
     assert np.array_equal(D1.cpu().numpy(), ref["D1"])
 
 
+@pytest.mark.parametrize("W,H,D,width,kind", [
+    (333, 130, 128, 17, "near_truth"), (250, 70, 256, 17, "random"), (181, 45, 64, 1, "random"),
+    (129, 100, 128, 16, "near_truth"), (300, 64, 128, 33, "random")])
+def test_all_tiles_banded_match_oracle(B, ctx, orc, W, H, D, width, kind):
+    """Every tile banded: the rows then run with one lane per row whenever the windows span at
+    most two 16-disparity groups (widths up to 17), across window moves of any size and rows
+    past the last warp's end."""
+    sc, left, right = _pair(W, H, 70 + W + width)
+    m = synth.true_model(sc)
+    kap_o = orc.kappa(orc.RoadModel.make(*m), W, H, 10.0)
+    centre = _tile_centres(sc, W, H, kap_o) if kind == "near_truth" else None
+    tl = _random_tiles(W, H, D, 12 + width, frac_full=0.0, centre=centre)
+    ref = orc.sgm_band(left, right, orc.RoadModel.make(*m), orc.Params(D=D, paths=8), tl, width)
+    _, d, D1 = B.pd_sgm_band(ctx, torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda(),
+                             B.RoadModel.make(*m), B.default_params(D=D), torch.from_numpy(tl).cuda(),
+                             width)
+    torch.cuda.synchronize()
+    assert np.array_equal(d.cpu().numpy(), ref["d_int"])
+    assert np.array_equal(D1.cpu().numpy(), ref["D1"])
+
+
 @pytest.mark.parametrize("width", [1, 5, 16, 33])
 def test_band_widths_match_oracle(B, ctx, orc, width):
     W, H, D = 150, 50, 64
