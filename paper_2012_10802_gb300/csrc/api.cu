@@ -322,6 +322,8 @@ void batch_enqueue(pd_ctx* ctx, const std::vector<WavePlan>& waves, char* table_
     BatchWaveDev d;
     char* base = table_dev + w.table_off;
     d.pairs = reinterpret_cast<const BatchPair*>(base + w.pairs_off);
+    d.host_pairs = reinterpret_cast<const BatchPair*>(static_cast<char*>(ctx->pinned) +
+                                                      w.table_off + w.pairs_off);
     for (int k = 0; k < kBatchStages; ++k) d.starts[k] = reinterpret_cast<const int*>(base + w.starts_off[k]);
     d.segs = reinterpret_cast<const BatchSegment*>(base + w.segs_off);
     d.counter = reinterpret_cast<unsigned int*>(base + w.counter_off);
@@ -507,6 +509,7 @@ extern "C" pd_status pd_sgm_batch(pd_ctx* ctx, const pd_pair* pairs, int n, cons
       BatchWaveDev d;
       char* base = table_dev + w.table_off;
       d.pairs = reinterpret_cast<const BatchPair*>(base + w.pairs_off);
+      d.host_pairs = nullptr;  // the aggregation alone needs no pair shapes on the host
       for (int k = 0; k < kBatchStages; ++k) d.starts[k] = reinterpret_cast<const int*>(base + w.starts_off[k]);
       d.segs = reinterpret_cast<const BatchSegment*>(base + w.segs_off);
       d.counter = reinterpret_cast<unsigned int*>(base + w.counter_off);

@@ -5,7 +5,10 @@
 // so the results are identical to one pd_sgm call per pair.  The aggregation is one persistent
 // launch: each warp repeatedly takes the next task (a group of lines of one pair and one
 // direction) from an atomic counter over a task list ordered longest-first, so short and long
-// lines of all pairs share the GPU.  No kernel waits on another block.
+// lines of all pairs share the GPU.  Eq. (9) is the exception: its blocks are short and wait on
+// DRAM, and the search for the pair (dependent loads before the first volume load) cost them
+// 15 % (8.6 against 7.4 ms over 64 mixed pairs), so it runs one launch per pair.  No kernel
+// waits on another block.
 #include "batch.cuh"
 #include "sgm_body.cuh"
 
@@ -121,16 +124,13 @@ __global__ void __launch_bounds__(256) k_aggregate_b(const BatchPair* __restrict
   }
 }
 
-__global__ void __launch_bounds__(kWtaThreads) k_wta_b(const BatchPair* __restrict__ pairs,
-                                                       const int* __restrict__ starts, int npairs,
-                                                       int ndirs) {
-  const int i = find_pair(starts, npairs, blockIdx.x);
+// Eq. (9) and the right view for pair i of the wave: one launch per pair, so a block needs no
+// search for its pair (the pair's row of the table is one load).
+__global__ void __launch_bounds__(kWtaThreads) k_wta_pair(const BatchPair* __restrict__ pairs,
+                                                          int i, int ndirs) {
   const BatchPair& p = pairs[i];
-  const int b = blockIdx.x - starts[i];
-  const int P = kWtaThreads / (p.D >> 4);
-  const int nbx = (p.W + P - 1) / P;
-  wta_block(p.vols, ndirs, p.vol_bytes, nullptr, p.W, p.D, p.d_int, p.dsub, p.rkeys, b % nbx,
-            b / nbx);
+  wta_block(p.vols, ndirs, p.vol_bytes, nullptr, p.W, p.D, p.d_int, p.dsub, p.rkeys, blockIdx.x,
+            blockIdx.y);
 }
 
 __global__ void k_lr_b(const BatchPair* __restrict__ pairs, const int* __restrict__ starts,
@@ -151,8 +151,6 @@ void batch_stage_blocks(int W, int H, int D, int counts[kBatchStages]) {
   counts[kStageCost] = cost_blocks_per_row(W, D) * H;
   const size_t N = (size_t)W * H;
   counts[kStageFill] = (int)((N + 4095) / 4096);
-  const int Pw = kWtaThreads / (D / 16);
-  counts[kStageWta] = ((W + Pw - 1) / Pw) * H;
   counts[kStageLr] = ((W + 255) / 256) * H;
 }
 
@@ -179,8 +177,12 @@ void launch_batch_wave(cudaStream_t s, const BatchWaveDev& w, int P1, int P2, in
   raise_smem_limit((const void*)k_aggregate_b, smem);
   k_aggregate_b<<<agg_blocks, agg_warps * 32, smem, s>>>(w.pairs, w.segs, w.nseg, w.ntasks,
                                                          w.counter, P1x2, K21x2);
-  k_wta_b<<<w.total[kStageWta], kWtaThreads, (size_t)kWtaThreads * 16 * sizeof(uint16_t), s>>>(
-      w.pairs, w.starts[kStageWta], n, paths);
+  for (int i = 0; i < n; ++i) {
+    const BatchPair& hp = w.host_pairs[i];
+    const int P = kWtaThreads / (hp.D / 16);
+    k_wta_pair<<<dim3((hp.W + P - 1) / P, hp.H), kWtaThreads, wta_smem_bytes(hp.D), s>>>(
+        w.pairs, i, paths);
+  }
   k_lr_b<<<w.total[kStageLr], 256, 0, s>>>(w.pairs, w.starts[kStageLr], n, lr_tol);
 }
 

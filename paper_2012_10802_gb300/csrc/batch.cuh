@@ -30,11 +30,13 @@ struct BatchSegment {
   int first, pair, r, dx, dy, pad;
 };
 
-enum { kStageKappa = 0, kStageCensus, kStageCost, kStageFill, kStageWta, kStageLr, kBatchStages };
+// Stages whose launch covers every pair of a wave (Eq. (9) runs one launch per pair).
+enum { kStageKappa = 0, kStageCensus, kStageCost, kStageFill, kStageLr, kBatchStages };
 
 // Device view of one wave: the tables live in the context scratch.
 struct BatchWaveDev {
   const BatchPair* pairs;
+  const BatchPair* host_pairs;      // the same table in host memory (shapes for per-pair grids)
   const int* starts[kBatchStages];  // per stage, npairs + 1 block prefixes
   const BatchSegment* segs;
   unsigned int* counter;

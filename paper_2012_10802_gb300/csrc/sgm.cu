@@ -421,7 +421,7 @@ void launch_wta(cudaStream_t s, const uint8_t* vols, int ndirs, size_t vol_bytes
   int G = D / 16;
   int P = kWtaThreads / G;
   dim3 grid((W + P - 1) / P, H);
-  size_t smem = (size_t)P * D * sizeof(uint16_t);
+  const size_t smem = wta_smem_bytes(D);
   k_wta<<<grid, kWtaThreads, smem, s>>>(vols, ndirs, vol_bytes, S, W, D, d_int, dsub, rkeys);
 }
 

@@ -97,15 +97,17 @@ __device__ __forceinline__ void census_tile(const uint8_t* __restrict__ img, int
 }
 
 // ----------------------------------------------------------------------------- cost
-// Interleaved layout, D % 16 == 0.  A block covers one segment of kCostSeg(D) pixels of a row
-// from one shared copy of the right codes it needs.  A warp computes one 16-disparity group for
-// 32 consecutive pixels (lane = pixel), so its shared reads are consecutive words at a constant
-// offset per disparity; the 16-byte results go through a swizzled shared tile and leave as
-// contiguous rows of the volume.
+// Interleaved layout, D % 16 == 0.  A block covers one segment of cost_seg(D) pixels of a row
+// from one shared copy of the codes it needs.  A lane computes one 16-disparity group g for four
+// consecutive pixels u .. u + 3: their right codes x = u + k - d, d in [16g, 16g + 16), are the 19
+// consecutive words ending at x = u + 3 - 16g, read as five aligned 16-byte shared loads (the
+// window starts at a multiple of 4 words because D and u - u0 are multiples of 4).  The lanes of
+// a warp take the groups as the slow index, so a warp's stores for one k cover whole 16-byte
+// chunks of D-byte pixel rows, and the window loads of 8 consecutive lanes fall in distinct
+// banks.
 constexpr int kCostThreads = 256;
 constexpr int kCostWarps = kCostThreads / 32;
 constexpr int kCostSlices = 8;
-constexpr int kCostStage = 8192;  // bytes of one pass: max(32, 256 / (D/16)) pixels x D bytes
 
 __host__ __device__ __forceinline__ int cost_seg(int D) {
   return kCostSlices * (kCostThreads / (D >> 4));
@@ -114,74 +116,72 @@ __host__ __device__ __forceinline__ int cost_blocks_per_row(int W, int D) {
   return (W + cost_seg(D) - 1) / cost_seg(D);
 }
 
-__device__ __forceinline__ uint32_t lds32(uint32_t addr) {
-  uint32_t v;
-  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
-  return v;
+// Bytes (a, b, c, d) of the low bytes of four values.
+__device__ __forceinline__ uint32_t pack4(uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  return __byte_perm(__byte_perm(a, b, 0x0040), __byte_perm(c, d, 0x0040), 0x5410);
 }
 
-// 16 costs of group g for pixel u (codes c0; the right code of d = 16g + dd at shared address
-// r - 4 dd): byte 2j holds d = 16g + j and byte 2j + 1 holds d = 16g + 8 + j.  CHECK: x = u - d
-// may be negative.
+// The 16 costs of group g for pixel u + k: word i holds d - 16g = 2i, 2i + 8, 2i + 1, 2i + 9 in
+// its bytes 0..3 (byte 2j: d = 16g + j, byte 2j + 1: d = 16g + 8 + j).  w[m] is the right code
+// of x = u + k - (16g + 15 + k - m), i.e. d - 16g = 15 + k - m.  CHECK: x may be negative
+// (x0 = u - 16g, the x of k = 0, d = 16g).
 template <bool CHECK>
-__device__ __forceinline__ uint4 cost16(uint32_t c0, uint32_t r, int x0) {
-  uint32_t w[4];
+__device__ __forceinline__ uint4 cost16_of(uint32_t c0, const uint32_t (&w)[20], int k, int x0) {
+  uint32_t c[16];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    uint32_t packed = 0;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int p = 4 * i + b;
-      const int dd = (p >> 1) + ((p & 1) << 3);  // d - 16g
-      uint32_t c = (uint32_t)__popc(c0 ^ lds32(r - 4u * (uint32_t)dd));
-      if (CHECK && x0 - dd < 0) c = (uint32_t)kCensusBits;
-      packed |= c << (8 * b);
-    }
-    w[i] = packed;
+  for (int dd = 0; dd < 16; ++dd) {
+    c[dd] = (uint32_t)__popc(c0 ^ w[15 + k - dd]);
+    if (CHECK && x0 + k - dd < 0) c[dd] = (uint32_t)kCensusBits;
   }
-  return make_uint4(w[0], w[1], w[2], w[3]);
+  return make_uint4(pack4(c[0], c[8], c[1], c[9]), pack4(c[2], c[10], c[3], c[11]),
+                    pack4(c[4], c[12], c[5], c[13]), pack4(c[6], c[14], c[7], c[15]));
 }
 
 // Interleaved cost of the segment bx of row v.
 __device__ __forceinline__ void cost_il_block(const uint32_t* __restrict__ cl,
                                               const uint32_t* __restrict__ cr, int W, int D,
                                               uint8_t* __restrict__ cost, int bx, int v) {
-  __shared__ uint32_t sR[kCostSlices * kCostThreads + kMaxD];
-  __shared__ __align__(16) uint4 stage[kCostStage / 16];
-  const int groups = D >> 4;
+  __shared__ __align__(16) uint32_t sR[kCostSlices * kCostThreads + kMaxD];
+  __shared__ __align__(16) uint32_t sL[kCostSlices * kCostThreads];
   const int seg = cost_seg(D);
   const int u0 = bx * seg;
   const int base = u0 - D + 1;  // x of sR[0]
-  for (int i = threadIdx.x; i < seg + D - 1; i += kCostThreads) {
+  // the windows reach sR[seg + D - 1] (the last lane's fifth load); codes outside [0, W) read 0
+  for (int i = threadIdx.x; i < seg + D; i += kCostThreads) {
     const int x = base + i;
     sR[i] = (x >= 0 && x < W) ? cr[(size_t)v * W + x] : 0u;
   }
+  for (int i = threadIdx.x; i < seg; i += kCostThreads) {
+    const int u = u0 + i;
+    sL[i] = u < W ? cl[(size_t)v * W + u] : 0u;
+  }
+  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int pix = kCostStage / D;     // pixels per pass (32 chunk rows of 16 B per group)
-  const int chunks = pix >> 5;        // 32-pixel chunks per pass
-  const int gmask = groups - 1;
-  const int lg = 31 - __clz(groups);  // groups is a power of two: shifts, not divisions
-  for (int p0 = u0; p0 < u0 + seg && p0 < W; p0 += pix) {
-    __syncthreads();  // sR filled / the previous pass copied out
-    for (int it = warp; it < chunks * groups; it += kCostWarps) {
-      const int g = it & gmask, ch = it >> lg;
-      const int r = ch * 32 + lane;  // pixel row within the pass
-      const int u = p0 + r;
-      const uint32_t c0 = u < W ? cl[(size_t)v * W + u] : 0u;
-      const uint32_t rp =
-          (uint32_t)__cvta_generic_to_shared(sR) + 4u * (uint32_t)((u - base) - 16 * g);
-      const int x0 = u - 16 * g;  // x of d = 16g
-      const bool check = p0 + ch * 32 - 16 * g - 15 < 0;  // warp-uniform
-      const uint4 val = check ? cost16<true>(c0, rp, x0) : cost16<false>(c0, rp, x0);
-      stage[r * groups + (g ^ (r & gmask))] = val;
+  const int cpw = 32 / (D >> 4);  // 4-pixel chunks per warp and pass
+  const int g = lane / cpw, ch = lane % cpw;
+  const int step = kCostWarps * cpw * 4;
+  for (int r = warp * cpw * 4 + 4 * ch; r < seg; r += step) {
+    const int u = u0 + r;
+    if (u >= W) break;  // later passes are further right
+    const uint4 cq = *reinterpret_cast<const uint4*>(sL + r);
+    const uint32_t c0[4] = {cq.x, cq.y, cq.z, cq.w};
+    const int wb = r + D - 16 - 16 * g;  // sR index of x = u - 16g - 15, a multiple of 4
+    uint32_t w[20];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const uint4 t = *reinterpret_cast<const uint4*>(sR + wb + 4 * q);
+      w[4 * q] = t.x;
+      w[4 * q + 1] = t.y;
+      w[4 * q + 2] = t.z;
+      w[4 * q + 3] = t.w;
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < pix * groups; i += kCostThreads) {
-      const int r = i >> lg, g = i & gmask;
-      const int u = p0 + r;
-      if (u < W)
-        *reinterpret_cast<uint4*>(cost + ((size_t)v * W + u) * D + 16 * g) =
-            stage[r * groups + (g ^ (r & gmask))];
+    const int x0 = u - 16 * g;
+    const bool check = x0 - 15 < 0;
+    uint8_t* dst = cost + ((size_t)v * W + u) * D + 16 * g;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint4 val = check ? cost16_of<true>(c0[k], w, k, x0) : cost16_of<false>(c0[k], w, k, x0);
+      if (u + k < W) *reinterpret_cast<uint4*>(dst + (size_t)k * D) = val;
     }
   }
 }
@@ -541,16 +541,24 @@ __device__ __forceinline__ void agg_row_half(const uint8_t* __restrict__ cost,
 constexpr int kWtaThreads = 128;
 
 // Loads this thread's 16 disparities of S as planar u16x2 pairs (d = 16g + j, 16g + 8 + j).
+// All directions' loads are issued before the first sum (ndirs is 4 or 8), so a thread has up to
+// 128 bytes in flight.
 __device__ __forceinline__ void load_S_il(const uint8_t* __restrict__ vols, int ndirs,
                                           size_t vol_bytes, size_t off, uint32_t sw[8]) {
+  uint4 a[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+    if (r < ndirs) a[r] = __ldcs(reinterpret_cast<const uint4*>(vols + (size_t)r * vol_bytes + off));
 #pragma unroll
   for (int j = 0; j < 8; ++j) sw[j] = 0;
-  for (int r = 0; r < ndirs; ++r) {
-    uint4 a = __ldcs(reinterpret_cast<const uint4*>(vols + (size_t)r * vol_bytes + off));
-    const uint32_t raw[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
-      sw[j] = __vadd2(sw[j], __byte_perm(raw[j >> 1], 0, (j & 1) ? 0x4342 : 0x4140));
+  for (int r = 0; r < 8; ++r) {
+    if (r < ndirs) {
+      const uint32_t raw[4] = {a[r].x, a[r].y, a[r].z, a[r].w};
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        sw[j] = __vadd2(sw[j], __byte_perm(raw[j >> 1], 0, (j & 1) ? 0x4342 : 0x4140));
+    }
   }
 }
 
@@ -573,25 +581,32 @@ __device__ __forceinline__ void planar_to_natural(const uint32_t sw[8], uint32_t
   }
 }
 
-// One block covers P = 128 / G pixels of one row; G = D / 16 threads per pixel.
+// One block covers P = kWtaThreads / G pixels of one row; G = D / 16 threads per pixel.
 // Writes d* (int16) and the sub-pixel value, and folds the right-view candidates of its pixels
-// into rkeys[v][x] = min over d of (S(x + d, d) << 8 | d) with one atomicMin per covered x.
+// into rkeys[v][x] = min over d of (S(x + d, d) << 8 | d): every thread folds the keys of its 16
+// disparities into a shared-memory minimum per column x = u - d, and the block then folds the
+// columns it touched into rkeys with one atomicMin each.
+// Shared memory: P * D u16 of S, then P + D - 1 u32 column minima (wta_smem_bytes).
 __device__ __forceinline__ void wta_block(const uint8_t* __restrict__ vols, int ndirs,
                                           size_t vol_bytes, const uint16_t* __restrict__ S, int W,
                                           int D, int16_t* __restrict__ d_int,
                                           float* __restrict__ dsub, uint32_t* __restrict__ rkeys,
                                           int bx, int v) {
-  extern __shared__ uint16_t sS[];  // [P][D]
+  extern __shared__ uint16_t sS[];  // [P][D], then the column minima
   const int G = D >> 4;
   const int P = kWtaThreads / G;
   const int u0 = bx * P;
   const int Peff = min(P, W - u0);
+  const int ncol = Peff + D - 1;  // columns u0 - D + 1 .. u0 + Peff - 1
+  uint32_t* sKey = reinterpret_cast<uint32_t*>(sS + P * D);
+  for (int i = threadIdx.x; i < ncol; i += kWtaThreads) sKey[i] = 0xffffffffu;
   const int pix = threadIdx.x / G, g = threadIdx.x % G;
   const int u = u0 + pix;
   uint32_t key = 0xffffffffu;
+  uint32_t sw[8];
   if (pix < Peff) {
     size_t off = ((size_t)v * W + u) * D + 16 * g;
-    uint32_t sw[8], o[8];
+    uint32_t o[8];
     if (S)
       load_S_nat(S, off, sw);
     else
@@ -608,7 +623,16 @@ __device__ __forceinline__ void wta_block(const uint8_t* __restrict__ vols, int 
     }
   }
   for (int o = 1; o < G; o <<= 1) key = min(key, __shfl_xor_sync(kFull, key, o, G));
-  __syncthreads();
+  __syncthreads();  // column minima initialised, S of the block's pixels in shared memory
+  if (pix < Peff) {
+    // column of disparity d: u - d, at sKey[pix + D - 1 - d]
+    uint32_t* col = sKey + (pix + D - 1 - 16 * g);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      atomicMin(col - j, ((sw[j] & 0xffffu) << 8) | (uint32_t)(16 * g + j));
+      atomicMin(col - j - 8, ((sw[j] >> 16) << 8) | (uint32_t)(16 * g + 8 + j));
+    }
+  }
   if (pix < Peff && g == 0) {
     int ds = (int)(key & 0xffu);
     float sub = (float)ds;
@@ -621,19 +645,18 @@ __device__ __forceinline__ void wta_block(const uint8_t* __restrict__ vols, int 
     d_int[(size_t)v * W + u] = (int16_t)ds;
     dsub[(size_t)v * W + u] = sub;
   }
-  // right view: x in [u0 - D + 1, u0 + Peff - 1], candidates d with u0 <= x + d < u0 + Peff
-  for (int i = threadIdx.x; i < Peff + D - 1; i += kWtaThreads) {
-    int x = u0 - D + 1 + i;
-    if (x < 0) continue;
-    int dlo = max(0, u0 - x);
-    int dhi = min(D - 1, u0 + Peff - 1 - x);
-    uint32_t best = 0xffffffffu;
-    for (int d = dlo; d <= dhi; ++d) {
-      uint32_t k = ((uint32_t)sS[(x + d - u0) * D + d] << 8) | (uint32_t)d;
-      best = k < best ? k : best;
-    }
-    if (dlo <= dhi) atomicMin(rkeys + (size_t)v * W + x, best);
+  __syncthreads();
+  for (int i = threadIdx.x; i < ncol; i += kWtaThreads) {
+    const int x = u0 - D + 1 + i;
+    const uint32_t k = sKey[i];
+    if (x >= 0 && k != 0xffffffffu) atomicMin(rkeys + (size_t)v * W + x, k);
   }
+}
+
+// Dynamic shared memory of wta_block for disparity range D.
+__host__ __device__ constexpr size_t wta_smem_bytes(int D) {
+  return (size_t)kWtaThreads * 16 * sizeof(uint16_t) +
+         (size_t)(kWtaThreads * 16 / D + D - 1) * sizeof(uint32_t);
 }
 
 __device__ __forceinline__ void lr_block(const int16_t* __restrict__ d_int,
