@@ -332,35 +332,28 @@ __global__ void k_centres_out(int n, const float* __restrict__ cx, const float* 
 // ------------------------------------------------------------------- Eqs. (14)-(17)
 constexpr int kBins = 257;  // k = 0..255 plus an overflow bin for everything at or above 32 px
 
-// Adds (1, a, b, a^2 + b^2) of the lanes sharing a bin into the shared histogram h, one pass per
-// distinct bin of the warp, lanes 0-3 adding the bin's four sums in one atomic instruction.  All
-// 32 lanes must call it.  The sums use the single-instruction warp reduction on
-// 32-bit values; a and b (D2 below 2^16 px) fit, a^2 + b^2 is split into 16/16/32-bit parts.
+// Adds (1, a, b, a^2 + b^2) of the lanes sharing a bin into the shared histogram h.  The lanes
+// of one bin form a group (match.any); each sum is one group-masked warp reduction, executed by
+// every group at once, and the group's lowest lane adds the four sums.  All 32 lanes must call
+// it.  The sums use the single-instruction warp reduction on 32-bit values; a and b (D2 below
+// 2^16 px) fit, a^2 + b^2 is split into 16/16/32-bit parts.
 __device__ void warp_hist(bool valid, int bin, long long a, long long b,
                           unsigned long long (*h)[4]) {
   const int lane = threadIdx.x & 31;
-  unsigned pending = __ballot_sync(0xffffffffu, valid);
+  const unsigned peers = __match_any_sync(0xffffffffu, valid ? bin : -1);
   const unsigned long long sq = (unsigned long long)(a * a + b * b);
-  while (pending) {
-    const int leader = __ffs(pending) - 1;
-    const int bl = __shfl_sync(0xffffffffu, bin, leader);
-    const bool mine = valid && bin == bl;
-    const unsigned peers = __ballot_sync(0xffffffffu, mine);
-    const int sa = __reduce_add_sync(0xffffffffu, mine ? (int)a : 0);
-    const int sb = __reduce_add_sync(0xffffffffu, mine ? (int)b : 0);
-    const unsigned s0 = __reduce_add_sync(0xffffffffu, mine ? (unsigned)(sq & 0xffffu) : 0u);
-    const unsigned s1 = __reduce_add_sync(0xffffffffu, mine ? (unsigned)((sq >> 16) & 0xffffu) : 0u);
-    const unsigned s2 = __reduce_add_sync(0xffffffffu, mine ? (unsigned)(sq >> 32) : 0u);
-    if (lane < 4) {  // the four sums of the bin, one lane each, in one atomic instruction
-      const unsigned long long ssq = (unsigned long long)s0 + ((unsigned long long)s1 << 16) +
-                                     ((unsigned long long)s2 << 32);
-      const unsigned long long val = lane == 0   ? (unsigned long long)__popc(peers)
-                                     : lane == 1 ? (unsigned long long)(long long)sa
-                                     : lane == 2 ? (unsigned long long)(long long)sb
-                                                 : ssq;
-      atomicAdd(&h[bl][lane], val);
-    }
-    pending &= ~peers;
+  const int sa = __reduce_add_sync(peers, (int)a);
+  const int sb = __reduce_add_sync(peers, (int)b);
+  const unsigned s0 = __reduce_add_sync(peers, (unsigned)(sq & 0xffffu));
+  const unsigned s1 = __reduce_add_sync(peers, (unsigned)((sq >> 16) & 0xffffu));
+  const unsigned s2 = __reduce_add_sync(peers, (unsigned)(sq >> 32));
+  if (valid && lane == __ffs(peers) - 1) {
+    const unsigned long long ssq = (unsigned long long)s0 + ((unsigned long long)s1 << 16) +
+                                   ((unsigned long long)s2 << 32);
+    atomicAdd(&h[bin][0], (unsigned long long)__popc(peers));
+    atomicAdd(&h[bin][1], (unsigned long long)(long long)sa);
+    atomicAdd(&h[bin][2], (unsigned long long)(long long)sb);
+    atomicAdd(&h[bin][3], ssq);
   }
 }
 
