@@ -21,49 +21,84 @@ using namespace body;
 // recurrence with L = infinity outside the window, and no masking is needed.
 constexpr uint32_t kOutCost = 255;
 
-// Interleaved cost of the groups meeting each pixel's window, for 128 pixels of row v per block:
-// two lanes per pixel, lane l computing the groups b + l, b + l + 2, ... (kOutCost outside the
-// window within those groups).
-constexpr int kCostBandPix = 128;
+// Interleaved cost of the groups meeting each pixel's window, for kCostBandPix pixels of row v
+// per block.  A thread takes four consecutive pixels (one window: a 16-pixel tile holds four such
+// chunks) and, as lane l of the chunk's pair, the groups b + l, b + l + 2, ... of the window
+// (kOutCost outside the window within those groups).  As in the full-range cost, the four pixels'
+// right codes for one group are 19 consecutive words, read as five aligned 16-byte shared loads.
+constexpr int kCostBandPix = 256;
 
-__global__ void __launch_bounds__(2 * kCostBandPix) k_cost_band(const uint32_t* __restrict__ cl,
-                                                                const uint32_t* __restrict__ cr,
-                                                                int W, int D, BandArgs band,
-                                                                size_t plane,
-                                                                uint8_t* __restrict__ cost) {
-  __shared__ uint32_t sR[kCostBandPix + kMaxD];
+// Bytes of word i (d - 16g = 2i, 2i + 8, 2i + 1, 2i + 9) set to 0xff where d is outside the
+// window (in16: bit dd set for d = 16g + dd inside it).
+__device__ __forceinline__ uint32_t out_bytes(uint32_t in16, int i) {
+  const uint32_t out = ~in16;
+  return (((out >> (2 * i)) & 1u) * 0xffu) | (((out >> (2 * i + 8)) & 1u) * 0xff00u) |
+         (((out >> (2 * i + 1)) & 1u) * 0xff0000u) | (((out >> (2 * i + 9)) & 1u) * 0xff000000u);
+}
+
+template <bool CHECK>
+__device__ __forceinline__ uint4 cost16_band(uint32_t c0, const uint32_t (&w)[20], int k, int x0,
+                                             const uint32_t (&om)[4]) {
+  uint32_t c[16];
+#pragma unroll
+  for (int dd = 0; dd < 16; ++dd) {
+    c[dd] = (uint32_t)__popc(c0 ^ w[15 + k - dd]);
+    if (CHECK && x0 + k - dd < 0) c[dd] = (uint32_t)kCensusBits;
+  }
+  return make_uint4(pack4(c[0], c[8], c[1], c[9]) | om[0], pack4(c[2], c[10], c[3], c[11]) | om[1],
+                    pack4(c[4], c[12], c[5], c[13]) | om[2], pack4(c[6], c[14], c[7], c[15]) | om[3]);
+}
+
+__global__ void __launch_bounds__(kCostBandPix / 2) k_cost_band(const uint32_t* __restrict__ cl,
+                                                              const uint32_t* __restrict__ cr,
+                                                              int W, int D, BandArgs band,
+                                                              size_t plane,
+                                                              uint8_t* __restrict__ cost) {
+  __shared__ __align__(16) uint32_t sR[kCostBandPix + kMaxD];
+  __shared__ __align__(16) uint32_t sL[kCostBandPix];
   const int v = blockIdx.y;
   const int u0 = blockIdx.x * kCostBandPix;
-  const int base = u0 - D + 1;
-  for (int i = threadIdx.x; i < kCostBandPix + D - 1; i += 2 * kCostBandPix) {
+  const int base = u0 - D + 1;  // x of sR[0]; the windows reach sR[kCostBandPix + D - 1]
+  for (int i = threadIdx.x; i < kCostBandPix + D; i += blockDim.x) {
     const int x = base + i;
     sR[i] = (x >= 0 && x < W) ? cr[(size_t)v * W + x] : 0u;
   }
+  for (int i = threadIdx.x; i < kCostBandPix; i += blockDim.x) {
+    const int u = u0 + i;
+    sL[i] = u < W ? cl[(size_t)v * W + u] : 0u;
+  }
   __syncthreads();
-  const int u = u0 + (threadIdx.x >> 1), l = threadIdx.x & 1;
+  const int r = 4 * (threadIdx.x >> 1), l = threadIdx.x & 1;  // chunk's first pixel, lane
+  const int u = u0 + r;
   if (u >= W) return;
   int lo, hi;
   band_window(band, u, v, D, lo, hi);
   const int e = (hi - 1) >> 4;
-  const uint32_t c0 = cl[(size_t)v * W + u];
+  const uint4 cq = *reinterpret_cast<const uint4*>(sL + r);
+  const uint32_t c0[4] = {cq.x, cq.y, cq.z, cq.w};
   for (int g = (lo >> 4) + l; g <= e; g += 2) {
-    uint32_t w[4];
+    const uint32_t in16 = group_in_mask(g, lo, hi);
+    const uint32_t om[4] = {out_bytes(in16, 0), out_bytes(in16, 1), out_bytes(in16, 2),
+                            out_bytes(in16, 3)};
+    const int wb = r + D - 16 - 16 * g;  // sR index of x = u - 16g - 15, a multiple of 4
+    uint32_t w[20];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      uint32_t packed = 0;
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int p = 4 * i + b;
-        const int d = 16 * g + (p >> 1) + ((p & 1) << 3);
-        const int x = u - d;
-        uint32_t c = x >= 0 ? (uint32_t)__popc(c0 ^ sR[x - base]) : (uint32_t)kCensusBits;
-        if (d < lo || d >= hi) c = kOutCost;
-        packed |= c << (8 * b);
-      }
-      w[i] = packed;
+    for (int q = 0; q < 5; ++q) {
+      const uint4 t = *reinterpret_cast<const uint4*>(sR + wb + 4 * q);
+      w[4 * q] = t.x;
+      w[4 * q + 1] = t.y;
+      w[4 * q + 2] = t.z;
+      w[4 * q + 3] = t.w;
     }
-    *reinterpret_cast<uint4*>(cost + plane * g + ((size_t)v * W + u) * 16) =
-        make_uint4(w[0], w[1], w[2], w[3]);
+    const int x0 = u - 16 * g;
+    const bool check = x0 - 15 < 0;
+    uint8_t* dst = cost + plane * g + ((size_t)v * W + u) * 16;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint4 val = check ? cost16_band<true>(c0[k], w, k, x0, om)
+                              : cost16_band<false>(c0[k], w, k, x0, om);
+      if (u + k < W) *reinterpret_cast<uint4*>(dst + 16 * k) = val;
+    }
   }
 }
 
@@ -535,7 +570,7 @@ __global__ void k_lr_band(const int16_t* __restrict__ d_int, const float* __rest
 
 void launch_cost_band(cudaStream_t s, const uint32_t* cl, const uint32_t* cr, int W, int H, int D,
                       const BandArgs& band, uint8_t* cost) {
-  k_cost_band<<<dim3((W + kCostBandPix - 1) / kCostBandPix, H), 2 * kCostBandPix, 0, s>>>(
+  k_cost_band<<<dim3((W + kCostBandPix - 1) / kCostBandPix, H), kCostBandPix / 2, 0, s>>>(
       cl, cr, W, D, band, (size_t)W * H * 16, cost);
 }
 
