@@ -423,6 +423,7 @@ extern "C" pd_status pd_sgm_batch(pd_ctx* ctx, const pd_pair* pairs, int n, cons
     struct Seg {
       BatchSegment s;
       int ntasks, nsteps;
+      long long work;  // the pair's W * H * D
     };
     std::vector<Seg> segs;
     size_t off = 0;
@@ -466,12 +467,16 @@ extern "C" pd_status pd_sgm_batch(pd_ctx* ctx, const pd_pair* pairs, int n, cons
         sg.s = BatchSegment{0, j, r, dx, dy, 0};
         sg.ntasks = (nlines + lpw - 1) / lpw;
         sg.nsteps = nsteps;
+        sg.work = (long long)q.W * q.H * q.D;
         segs.push_back(sg);
       }
       sig.insert(sig.end(), {q.W, q.H, q.D, (long long)q.pitch});
     }
-    std::stable_sort(segs.begin(), segs.end(),
-                     [](const Seg& a, const Seg& b) { return a.nsteps > b.nsteps; });
+    // pair by pair, the largest first, all directions of a pair together: a pair's tasks then run
+    // at the same time, and its directions that sweep the same rows read them while L2 holds them
+    std::stable_sort(segs.begin(), segs.end(), [](const Seg& a, const Seg& b) {
+      return a.work != b.work ? a.work > b.work : a.s.pair < b.s.pair;
+    });
     BatchSegment* hs = reinterpret_cast<BatchSegment*>(hbase + w.segs_off);
     int first = 0;
     for (size_t k = 0; k < segs.size(); ++k) {
