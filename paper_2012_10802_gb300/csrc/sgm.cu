@@ -112,6 +112,11 @@ __device__ __forceinline__ int middle_out(int r, int n) {
 }
 
 constexpr int kAggPWarps = 4;               // warps per block of the persistent aggregation
+// The walkers of lines shorter than the rows sleep this long per step, so that the rows (the
+// critical path of a landscape frame) that share their schedulers issue sooner: diagonals
+// always, columns when H < W.  At 720p, D = 128 the aggregation took 0.328-0.330 ms with 16-48
+// ns against 0.338 ms with none, and 0.346 ms with 200 ns.
+constexpr unsigned kAggYieldNs = 32;
 constexpr int kAggPRingUint4 = 512;         // 8 KB ring per warp
 
 // Persistent aggregation of Eq. (8) over all directions of a frame.  Each warp repeatedly takes
@@ -161,10 +166,16 @@ __global__ void __launch_bounds__(kAggPWarps * 32) k_aggregate_p(
       else
         agg_walk<GH, 1, true>(cost, dst, W, H, D, dx, 0, P1x2, K21x2, k * (32 / GH), ring);
     }
-    else if (cls == 1)
-      agg_walk<GO, 2, true>(cost, dst, W, H, D, 0, dy, P1x2, K21x2, k * (32 / GO), ring);
+    else if (cls == 1) {
+      if (H < W)  // columns shorter than the rows
+        agg_walk<GO, 2, true, kAggYieldNs>(cost, dst, W, H, D, 0, dy, P1x2, K21x2, k * (32 / GO),
+                                           ring);
+      else
+        agg_walk<GO, 2, true>(cost, dst, W, H, D, 0, dy, P1x2, K21x2, k * (32 / GO), ring);
+    }
     else
-      agg_walk<GO, 2, false>(cost, dst, W, H, D, dx, dy, P1x2, K21x2, k * (32 / GO), ring);
+      agg_walk<GO, 2, false, kAggYieldNs>(cost, dst, W, H, D, dx, dy, P1x2, K21x2, k * (32 / GO),
+                                          ring);
   }
 }
 

@@ -291,7 +291,7 @@ __device__ __forceinline__ uint32_t group_in_mask(int g, int lo, int hi) {
 // needs half the lanes, shuffles and per-step bookkeeping of one group per lane.  FULL: every
 // line of the warp lies inside the image at every step (rows and columns), so a lane is active
 // for the whole walk when its line exists and the per-step activity tests and state resets go.
-template <int G, int NG, bool FULL>
+template <int G, int NG, bool FULL, unsigned YIELD_NS = 0>
 __device__ __forceinline__ void agg_walk(const uint8_t* __restrict__ cost,
                                          uint8_t* __restrict__ dst_vol, int W, int H, int D,
                                          int dx, int dy, uint32_t P1x2, uint32_t K21x2, int first,
@@ -340,6 +340,9 @@ __device__ __forceinline__ void agg_walk(const uint8_t* __restrict__ cost,
     // rows and columns: a lane is active exactly when its line exists; diagonals: inside the
     // common range every lane is (all its lines exist there)
     const bool act = FULL ? lvalid : (ALL || (s >= lw.s_first && s <= lw.s_last));
+    // YIELD_NS > 0: the walker sleeps that long each step, leaving its scheduler's issue slots
+    // to the longer chains that share it
+    if constexpr (YIELD_NS > 0) __nanosleep(YIELD_NS);
     cp_async_wait<ST - 2>();  // the copy of step s is complete
     uint32_t raw[4 * NG];
 #pragma unroll
