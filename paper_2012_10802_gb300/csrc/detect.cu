@@ -568,11 +568,15 @@ int launch_threshold(cudaStream_t s, const float* D2, const float* D1, const flo
   float* thr_up = c.take<float>(1);
   if (thresholds) thr = thresholds;
   cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * 2 * kBins * 4, s);
-  // about 8 resident blocks per SM: each warp's per-bin loop is a latency chain, so the kernel
-  // needs many of them in flight
+  // one full wave of 8 resident blocks per SM (the register limit at 256 threads): many warps
+  // in flight, and no second wave of a few blocks (rounding the grid up made one, of 4 blocks
+  // at 720p, that doubled the kernel's time)
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int xb = (W + 255) / 256;
-  int yb = (8 * 152 + xb - 1) / xb;
-  yb = yb < H ? yb : H;
+  int yb = (8 * (sms > 0 ? sms : 1)) / xb;
+  yb = yb < 1 ? 1 : (yb < H ? yb : H);
   k_thresh_hist<<<dim3(xb, yb), 256, 0, s>>>(D2, D1, W, H, hist);
   k_thresh_solve<<<1, kSolveThreads, 0, s>>>(hist, delta_pd, mode, thr, thr_up, E2);
   size_t N = (size_t)W * H;
