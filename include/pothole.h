@@ -325,8 +325,9 @@ typedef struct {
 pd_status pd_batch_config(pd_ctx* ctx, size_t scratch_budget_bytes, int use_graph, int autotune);
 
 /* Sec. II-A and II-B for n pairs of any sizes and disparity ranges with one launch per stage and
- * wave; the aggregation is one persistent launch whose warps take line groups of all pairs from a
- * shared counter, longest lines first.  Results are identical to n pd_sgm calls.
+ * wave (Eq. (9): one launch per pair); the aggregation is one persistent launch whose warps take
+ * line groups from a shared counter over a task list ordered pair by pair, the largest pair
+ * first.  Results are identical to n pd_sgm calls.
  * pairs: host array of n descriptors; params: host (paths, P1, P2, lr_tol, delta_pt are used; D
  * is per pair).  The call returns after enqueueing; it waits for the previous batch on this
  * context to pass its table upload before reusing the host staging buffer. */
